@@ -1,0 +1,350 @@
+"""Benchmark: batched reflectivity log-likelihood + exact gradient on GB300.
+
+Metric: forward+gradient (sample x Q-node) evaluations per second, where one
+evaluation is one (stack, Q point, quadrature node) triple of a
+nr_loglik_grad call.  Workload (default): the thick-oxide film fit --
+16384 parameter samples of a 1-layer 1000-3000 A film on Si, 400 Q points in
+[0.005, 0.25] 1/A, dQ/Q = 3 % FWHM, 21 Gauss-Hermite nodes (137.6 M
+evaluations per step), data from the CPU oracle x lognormal 5 % noise.
+
+One step = one nr_loglik_grad call over the whole batch (inputs resident in
+HBM).  Between timed steps L2 is flushed by writing a 512 MiB buffer; each
+step is timed with CUDA events on the launching stream.  `e2e` repeats the
+measurement through the C-ABI call with pinned HOST buffers (the library's
+H2D copies, compute and D2H copies inside the timed call).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--no-cpu-baseline]
+
+`--impl reference` times the plain CPU oracle on the host cores (there is
+no reference implementation of this method to run): a bounded sample of the
+same workload per step.  Under torchrun (N > 1) each rank runs its own
+seeded copy of the workload (weak scaling, no collective in the data path);
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+grad (sample x Q-node) evals/s"
+UNIT = "evals/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def flops_per_eval(n: int, absorbing: bool, K: int) -> float:
+    """Algorithmic FP32 flops of one fwd+grad evaluation of an n-layer stack
+    (FMA = 2), counted from the kernel source; the table and its derivation
+    are in the design notes.  Transcendental (XU) ops are not counted."""
+    med = 28 if absorbing else 24          # k_j: double-float k0^2 - c_j, rsqrt, Newton step
+    fres = 33                              # r_j with Nevot-Croce factor
+    phase = 22                             # E_j: double-float phase, mod-2pi reduction
+    mob = 26                               # Parratt / Moebius step
+    fwd = 26 + (n + 1) * (med + fres) + n * (phase + mob)
+    adj = 3 + 83 * n + 74 * (n + 1)
+    if n > 2:                              # deeper stacks recompute k, r, E in the adjoint
+        adj += (n + 1) * (med + fres) + n * (phase + 12)
+    per_q = (K + 15.0) / K + 2.0           # smearing sum, likelihood, seeds
+    return float(fwd + adj + per_q)
+
+
+def peak_fp32_tflops(mhz: float = SM_MAX_MHZ_NOMINAL) -> float:
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_from_profile(kernel_src: str, profile_txt: str):
+    """DRAM bytes per launch recorded with ncu for the current kernel source,
+    or None when the source changed since the capture."""
+    try:
+        want = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        rec = {}
+        for line in open(profile_txt):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+        if rec.get("kernel source sha256[:16]") != want:
+            return None
+        return float(rec["dram bytes per full launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def cpu_baseline(wl, target_s: float = 10.0) -> dict:
+    """The CPU oracle as it stands, on the host cores, on a bounded sample of
+    the workload's stacks (fwd + exact dual-number gradient)."""
+    import oracle
+    threads = oracle.max_threads()
+    probe = max(1, min(wl.n_stacks, threads))
+    sub = wl.subset(np.arange(probe))
+    t0 = time.perf_counter()
+    oracle.batch("grad", sub.n_layers, sub.params, sub.dataset, sub.q_off, sub.q, sub.dq, sub.r_obs, sub.r_err,
+                 sub.n_quad)
+    dt = time.perf_counter() - t0
+    count = int(min(wl.n_stacks, max(probe, probe * target_s / max(dt, 1e-6))))
+    count = max(probe, count // threads * threads) if count >= threads else count
+    sub = wl.subset(np.arange(count))
+    t0 = time.perf_counter()
+    oracle.batch("grad", sub.n_layers, sub.params, sub.dataset, sub.q_off, sub.q, sub.dq, sub.r_obs, sub.r_err,
+                 sub.n_quad)
+    dt = time.perf_counter() - t0
+    return {"value": sub.evals / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {count} of {wl.n_stacks} stacks ({sub.evals} evals, {dt:.1f} s, fwd + dual-number grad)"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle (the only other implementation of the
+    method here), timed per step on a bounded sample of the workload."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2509_06924_gb300 import workloads as W
+    wl = W.make_workload(args.workload)
+    threads = oracle.max_threads()
+    # size one step to ~0.1 s of wall time so the whole run stays short
+    probe = wl.subset(np.arange(max(1, min(wl.n_stacks, threads))))
+    t0 = time.perf_counter()
+    oracle.batch("grad", probe.n_layers, probe.params, probe.dataset, probe.q_off, probe.q, probe.dq, probe.r_obs,
+                 probe.r_err, probe.n_quad)
+    dt = time.perf_counter() - t0
+    count = int(max(1, min(wl.n_stacks, probe.n_stacks * 0.1 / max(dt, 1e-6))))
+    sub = wl.subset(np.arange(count))
+
+    def step():
+        oracle.batch("grad", sub.n_layers, sub.params, sub.dataset, sub.q_off, sub.q, sub.dq, sub.r_obs, sub.r_err,
+                     sub.n_quad)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = sub.evals / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "stacks_per_step": count, "q_points": int(wl.q_off[-1]),
+                       "quad_nodes": wl.n_quad},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"first {count} of {wl.n_stacks} stacks per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2509_06924_gb300 as nr
+    from paper_2509_06924_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    wl = W.make_workload(args.workload, n_stacks=args.stacks, seed_offset=rank)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    batch = nr.Batch.from_workload(wl, device=dev)
+    ctx.plan(batch)
+    info = ctx.plan_info(batch)
+    ll = torch.empty(wl.n_stacks, dtype=torch.float64, device=dev)
+    g = torch.empty(batch.params.numel(), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.loglik_grad(batch, ll_out=ll, grad_out=g, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if ctx.device_status() != 0:
+        raise RuntimeError("device status flags raised during warm-up")
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))           # L2 flush outside the timed events
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if ws > 1:
+        dist.barrier()
+    per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(per_step) / len(per_step)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    evals = wl.evals
+    value = ws * evals / (ms * 1e-3)
+
+    # e2e: the same call with pinned host buffers (H2D + compute + D2H inside)
+    e2e = None
+    if not args.no_e2e:
+        hbatch = nr.Batch.from_workload(wl, device="cpu", pin=True)
+        hll = torch.empty(wl.n_stacks, dtype=torch.float64).pin_memory()
+        hg = torch.empty(hbatch.params.numel(), dtype=torch.float64).pin_memory()
+        for _ in range(3):
+            ctx.loglik_grad(hbatch, ll_out=hll, grad_out=hg)
+        e2e_steps = max(5, min(args.steps, 50))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.loglik_grad(hbatch, ll_out=hll, grad_out=hg)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        h2d = wl.params.nbytes + wl.q.nbytes + wl.dq.nbytes + wl.r_obs.nbytes + wl.r_err.nbytes
+        d2h = hll.numel() * 8 + hg.numel() * 8
+        e2e = {"value": ws * wl.evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    status = ctx.device_status()
+    if status != 0:
+        raise RuntimeError(f"device status flags {status}")
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return 0
+
+    absorbing = bool(np.any(wl.params[np.concatenate([np.arange(po + 2 * n + 2, po + 3 * n + 3)
+                                                      for po, n in zip(wl.par_off[:-1], wl.n_layers)])] > 0))
+    flops = sum(flops_per_eval(int(n), absorbing, wl.n_quad) * (wl.out_off[s + 1] - wl.out_off[s]) * wl.n_quad
+                for s, n in enumerate(wl.n_layers))
+    kernel_ms = ms  # the step is one launch of the gradient kernel per layer bucket
+    achieved = flops / (kernel_ms * 1e-3) / 1e12
+    peak = peak_fp32_tflops()
+    traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2509_06924_gb300", "csrc", "nr_mixed.cu"),
+                                    os.path.join(ROOT, "profiles", f"nr_mixed_grad_{args.workload}.txt"))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (double-float guards, f64 reductions)", "data": "synthetic",
+        "config": {"workload": args.workload, "stacks": wl.n_stacks, "q_points": int(wl.q_off[-1]),
+                   "quad_nodes": wl.n_quad, "layers": sorted(set(int(x) for x in wl.n_layers))[:4],
+                   "evals_per_step": evals, "l2": "flushed between steps (512 MiB write)",
+                   "launch": info},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)"},
+        "e2e": e2e,
+        "gpu_launches": int(info["launches"]) * args.steps,
+        "clocks": clk.summary(),
+        "wall_s_timed_region": t_wall,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="thick_oxide")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement (profiling runs)")
+    ap.add_argument("--stacks", type=int, default=None,
+                    help="override the stack count (small profiling cases; not a bench line)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

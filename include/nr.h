@@ -1,0 +1,173 @@
+/*
+ * nr.h -- C ABI of the GB300 (sm_103a) batched neutron-reflectivity library.
+ *
+ * The library evaluates, for a batch of layered slab models ("stacks"), the
+ * specular reflectivity, the Gaussian log-likelihood of observed data, and
+ * the exact gradient of that log-likelihood with respect to every slab and
+ * instrument parameter -- the quantities that gradient-based optimisation,
+ * Hamiltonian Monte-Carlo and variational inference evaluate at every step
+ * in arXiv 2509.06924 (Secs. 2.2-2.4; the forward model of Sec. 2.1 and the
+ * refjax kernel interface of Sec. 3).
+ *
+ * Physics (the paper names the Abeles matrix formalism, Sec. 2.1, and
+ * Gaussian interfacial roughness, Sec. 3, but prints no equation; these are
+ * the readings this library implements):
+ *   media j = 0 (fronting) .. n+1 (backing), layers j = 1..n;
+ *   k_0 = q/2,  k_j = sqrt(k_0^2 - 4 pi (rho_j - rho_0) + 4 pi i iota_j),
+ *     principal root (Im k_j >= 0);
+ *   r_j = (k_j - k_{j+1}) / (k_j + k_{j+1}) * exp(-2 k_j k_{j+1} sigma_j^2)
+ *     (Nevot-Croce), j = 0..n;
+ *   amplitude r = M_10 / M_00 of M = C_0 C_1 ... C_n with
+ *     C_j = [[e^{-i b_j}, r_j e^{-i b_j}], [r_j e^{i b_j}, e^{i b_j}]],
+ *     b_0 = 0, b_j = k_j d_j (equivalently the Parratt recursion);
+ *   R(q) = |r|^2;
+ *   smearing with a pointwise FWHM dQ (Sec. 3 smearing kernels; Sec. 4.1
+ *     pointwise FWHM): S(Q) = sum_k w_k R(Q + dQ x_k / (2 sqrt(ln 2))),
+ *     (x_k, sqrt(pi) w_k) the K-point Gauss-Hermite rule;
+ *   model m = scale * S + bkg (instrument parameters, Sec. 2.1);
+ *   loglik = -1/2 sum_i [((m_i - R_i)/e_i)^2 + ln(2 pi e_i^2)] (Gaussian
+ *     likelihood with count-derived deviations, Sec. 2.1; chi^2 of Eq. 20).
+ *
+ * Packed parameters of one stack with n layers: 4n+6 doubles
+ *     d[n] | rho[n+2] | iota[n+1] | sigma[n+1] | scale | bkg
+ *   d: thicknesses (A) of layers 1..n; rho: SLD (absolute A^-2, e.g.
+ *   2.07e-6 for Si) of fronting, layers, backing; iota: absorption
+ *   (imaginary SLD, >= 0) of layers and backing (the fronting medium is
+ *   non-absorbing); sigma: roughness (A) of interfaces 0..n, top to bottom.
+ *   Stacks are packed back to back in stack order.
+ *
+ * Conventions of every call:
+ *   - All calls return nr_status; on failure nr_last_error() gives a
+ *     message (thread-local, valid until the next call on that thread).
+ *   - Metadata arrays (n_layers, dataset, q_off) are HOST memory; bulk
+ *     arrays (params, q, dq, r_obs, r_err) and outputs are DEVICE memory
+ *     when batch->memory == NR_MEM_DEVICE, HOST memory (preferably pinned)
+ *     when batch->memory == NR_MEM_HOST.  The library never frees or
+ *     retains caller memory; host metadata is copied into the plan.
+ *   - Device-memory calls are asynchronous on `stream` (a cudaStream_t,
+ *     NULL = legacy default stream).  Host-memory calls copy in, compute
+ *     and copy out on `stream` and return after the stream is synchronised.
+ *   - Metadata is validated on the host (NR_EINVAL).  Problems that are only
+ *     visible in device data (non-finite parameters, a quadrature node at
+ *     q <= 0, e <= 0) never trap the GPU: the affected outputs become NaN
+ *     and a sticky device flag is raised, read by nr_device_status().
+ *   - A context is bound to the device that was current at nr_create and
+ *     is not thread-safe; use one context per host thread.
+ */
+#ifndef NR_H_
+#define NR_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NR_MAX_LAYERS 64 /* n_layers in [0, NR_MAX_LAYERS]                  */
+#define NR_MAX_QUAD 32   /* quadrature nodes K in [1, NR_MAX_QUAD]          */
+
+typedef enum {
+    NR_OK = 0,
+    NR_EINVAL = 1,     /* bad argument or metadata                            */
+    NR_ENOMEM = 2,     /* device or pinned-host allocation failed             */
+    NR_ECUDA = 3,      /* a CUDA runtime call failed (message has the name)   */
+    NR_ETIMEOUT = 4,   /* reserved: a bounded device wait gave up             */
+    NR_ENONFINITE = 5  /* device data produced a non-finite or invalid value  */
+} nr_status;
+
+typedef enum {
+    NR_MIXED = 0,      /* FP32 bulk with double-float guards (the fast path)  */
+    NR_FP64_PLAIN = 1  /* plain FP64 forward; gradient by central differences */
+} nr_precision;
+
+typedef enum { NR_MEM_DEVICE = 0, NR_MEM_HOST = 1 } nr_memory;
+
+/* Device status flags returned by nr_device_status (bitwise OR). */
+#define NR_FLAG_NONFINITE_PARAM 1 /* a parameter was NaN/Inf                 */
+#define NR_FLAG_BAD_Q 2           /* a quadrature node fell at q <= 0        */
+#define NR_FLAG_BAD_ERR 4         /* an uncertainty e_i was <= 0 or NaN      */
+
+typedef struct nr_options {
+    int32_t n_quad;        /* K quadrature nodes (default 17 when 0)          */
+    int32_t precision;     /* nr_precision                                    */
+    int32_t deterministic; /* 1: bitwise-reproducible reductions (default 1)  */
+    int32_t autotune;      /* 1: nr_plan times launch shapes and caches them  */
+    int32_t tile_q;        /* override: Q points per CTA tile (0 = auto)      */
+    int32_t chunk_q;       /* override: Q points per work item (0 = auto)     */
+    int32_t grid_ctas;     /* override: persistent CTAs (0 = auto)            */
+    int32_t reserved;
+} nr_options;
+
+typedef struct nr_batch {
+    int32_t n_stacks;         /* S >= 0                                       */
+    int32_t n_datasets;       /* D >= 1 when S > 0                            */
+    const int32_t *n_layers;  /* HOST [S]: layers of each stack               */
+    const int32_t *dataset;   /* HOST [S]: dataset (Q grid + data) of a stack */
+    const int64_t *q_off;     /* HOST [D+1]: dataset d owns points
+                                 [q_off[d], q_off[d+1]); q_off[0] = 0         */
+    int32_t memory;           /* nr_memory of the bulk arrays and outputs     */
+    int32_t reserved;
+    const double *params;     /* [sum_s (4 n_s + 6)] packed parameters        */
+    const float *q;           /* [q_off[D]] momentum transfer Q > 0 (1/A)     */
+    const float *dq;          /* [q_off[D]] resolution FWHM dQ >= 0 (1/A)     */
+    const float *r_obs;       /* [q_off[D]] observed reflectivity (loglik*)   */
+    const float *r_err;       /* [q_off[D]] its standard deviation e > 0      */
+} nr_batch;
+
+typedef struct nr_ctx nr_ctx;
+
+/* Create a context on the current CUDA device.  opt may be NULL (defaults).
+ * Allocates the context's device status word and computes the quadrature
+ * rule.  Errors: NR_EINVAL (bad options), NR_ECUDA, NR_ENOMEM. */
+nr_status nr_create(nr_ctx **out, const nr_options *opt);
+
+/* Release the context, its plans and workspaces (synchronises the device). */
+void nr_destroy(nr_ctx *ctx);
+
+/* Message of the last non-OK status returned on this thread. */
+const char *nr_last_error(void);
+
+/* Validate the batch metadata, build its work list on the device and, when
+ * the context was created with autotune = 1, time candidate launch shapes
+ * on the batch's own data.  Optional: the compute calls plan on first use.
+ * Must precede CUDA-graph capture of a compute call, which then allocates
+ * nothing and copies no metadata.  Errors: NR_EINVAL, NR_ENOMEM, NR_ECUDA. */
+nr_status nr_plan(nr_ctx *ctx, const nr_batch *batch);
+
+/* Smeared model m = scale * S(Q_i) + bkg for every stack and Q point of its
+ * dataset.  r_out: [sum_s len(dataset(s))] floats, stack-major, in stack
+ * order (stack s starts at the sum of the dataset lengths of stacks < s).
+ * Forward model of Sec. 2.1 with the smearing of Sec. 3. */
+nr_status nr_reflectivity(nr_ctx *ctx, const nr_batch *batch, float *r_out, void *stream);
+
+/* Gaussian log-likelihood of each stack against its dataset (Sec. 2.1;
+ * chi^2 term of Eq. 20).  loglik: [S] doubles.  r_obs and r_err required. */
+nr_status nr_loglik(nr_ctx *ctx, const nr_batch *batch, double *loglik, void *stream);
+
+/* Log-likelihood and its gradient w.r.t. all packed parameters (the exact
+ * gradient of Secs. 2.2-3; hand-written adjoint under NR_MIXED, central
+ * differences of the FP64 forward under NR_FP64_PLAIN).  grad: packed
+ * exactly like params.  Either output pointer may be NULL. */
+nr_status nr_loglik_grad(nr_ctx *ctx, const nr_batch *batch, double *loglik, double *grad,
+                         void *stream);
+
+/* Synchronise `stream`, return the sticky device flags raised since the
+ * last call (NR_FLAG_*) in *flags and clear them.  Returns NR_ENONFINITE
+ * when any flag was set, NR_OK otherwise. */
+nr_status nr_device_status(nr_ctx *ctx, void *stream, int32_t *flags);
+
+/* The library's own K-point Gauss-Hermite rule for exp(-x^2) (host
+ * computation; x and w are HOST arrays of K doubles). */
+nr_status nr_quadrature(int32_t K, double *x, double *w);
+
+/* Evaluations (stack x Q point x quadrature node) one compute call performs
+ * on this batch, and the launch shape last chosen for it (for reporting).
+ * Any output pointer may be NULL. */
+nr_status nr_plan_info(nr_ctx *ctx, const nr_batch *batch, int64_t *evals, int32_t *tile_q,
+                       int32_t *chunk_q, int32_t *grid_ctas, int32_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NR_H_ */

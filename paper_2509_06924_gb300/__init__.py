@@ -1,2 +1,314 @@
-"""GB300-native batched neutron-reflectivity forward model, log-likelihood and
-exact gradient (arXiv 2509.06924) behind a C-ABI library."""
+"""GB300-native batched neutron reflectometry: the forward reflectivity model,
+its Gaussian log-likelihood and the exact gradient of that log-likelihood
+(arXiv 2509.06924: Abeles forward model, Sec. 2.1; refjax kernel interface and
+smearing, Sec. 3; chi^2 / Gaussian likelihood, Eq. 20 and Sec. 2.1), for many
+parameter samples at once, as HMC and variational inference need them.
+
+This module is the thin Python binding of the C-ABI library ``libnr.so``
+(include/nr.h): it marshals numpy / torch buffers into the C structs and
+calls the library; every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: without the compiled library (or without
+a CUDA device) the calls raise.
+
+    import paper_2509_06924_gb300 as nr
+    ctx = nr.Context(n_quad=21)                       # NR_MIXED precision
+    batch = nr.Batch.from_workload(wl, device="cuda")  # device tensors
+    ll, grad = ctx.loglik_grad(batch)                 # torch float64 on device
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+NR_OK, NR_EINVAL, NR_ENOMEM, NR_ECUDA, NR_ETIMEOUT, NR_ENONFINITE = range(6)
+NR_MIXED, NR_FP64_PLAIN = 0, 1
+NR_MEM_DEVICE, NR_MEM_HOST = 0, 1
+NR_FLAG_NONFINITE_PARAM, NR_FLAG_BAD_Q, NR_FLAG_BAD_ERR = 1, 2, 4
+MAX_LAYERS = 64
+MAX_QUAD = 32
+EXPORTS = ("nr_create", "nr_destroy", "nr_last_error", "nr_plan", "nr_reflectivity", "nr_loglik",
+           "nr_loglik_grad", "nr_device_status", "nr_quadrature", "nr_plan_info")
+
+
+class NRError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"nr status {status}: {message}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("n_quad", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("tile_q", ctypes.c_int32), ("chunk_q", ctypes.c_int32),
+                ("grid_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class CBatch(ctypes.Structure):
+    _fields_ = [("n_stacks", ctypes.c_int32), ("n_datasets", ctypes.c_int32),
+                ("n_layers", ctypes.c_void_p), ("dataset", ctypes.c_void_p), ("q_off", ctypes.c_void_p),
+                ("memory", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("params", ctypes.c_void_p), ("q", ctypes.c_void_p), ("dq", ctypes.c_void_p),
+                ("r_obs", ctypes.c_void_p), ("r_err", ctypes.c_void_p)]
+
+
+_LIB = None
+_LIB_LOCK = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libnr.so (building it first when it is missing or stale)."""
+    global _LIB
+    with _LIB_LOCK:
+        if _LIB is None:
+            if build_if_missing:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"the CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
+            lib = ctypes.CDLL(_build.LIB)
+            vp, i32, i64p = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.nr_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Options)]
+            lib.nr_create.restype = ctypes.c_int
+            lib.nr_destroy.argtypes = [vp]
+            lib.nr_destroy.restype = None
+            lib.nr_last_error.argtypes = []
+            lib.nr_last_error.restype = ctypes.c_char_p
+            lib.nr_plan.argtypes = [vp, ctypes.POINTER(CBatch)]
+            lib.nr_reflectivity.argtypes = [vp, ctypes.POINTER(CBatch), vp, vp]
+            lib.nr_loglik.argtypes = [vp, ctypes.POINTER(CBatch), vp, vp]
+            lib.nr_loglik_grad.argtypes = [vp, ctypes.POINTER(CBatch), vp, vp, vp]
+            lib.nr_device_status.argtypes = [vp, vp, i32p]
+            lib.nr_quadrature.argtypes = [i32, dp, dp]
+            lib.nr_plan_info.argtypes = [vp, ctypes.POINTER(CBatch), i64p, i32p, i32p, i32p, i32p]
+            for name in EXPORTS:
+                if name not in ("nr_destroy", "nr_last_error"):
+                    getattr(lib, name).restype = ctypes.c_int
+            _LIB = lib
+        return _LIB
+
+
+def _check(status: int) -> None:
+    if status != NR_OK:
+        raise NRError(status, load_library(False).nr_last_error().decode(errors="replace"))
+
+
+def quadrature(K: int):
+    """The library's K-point Gauss-Hermite rule for exp(-x^2) (host call)."""
+    x = np.zeros(K)
+    w = np.zeros(K)
+    _check(load_library().nr_quadrature(K, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return x, w
+
+
+@dataclasses.dataclass
+class Batch:
+    """A batch of stacks: host metadata (numpy) plus bulk arrays that are
+    either torch tensors on a CUDA device or (pinned) host tensors."""
+    n_layers: np.ndarray
+    dataset: np.ndarray
+    q_off: np.ndarray
+    params: object
+    q: object
+    dq: object
+    r_obs: object = None
+    r_err: object = None
+
+    @property
+    def n_stacks(self) -> int:
+        return int(self.n_layers.size)
+
+    @property
+    def n_datasets(self) -> int:
+        return int(self.q_off.size - 1)
+
+    @property
+    def on_host(self) -> bool:
+        return not self.params.is_cuda
+
+    @property
+    def total_out(self) -> int:
+        lens = (self.q_off[1:] - self.q_off[:-1])[self.dataset]
+        return int(lens.sum())
+
+    @staticmethod
+    def from_arrays(n_layers, dataset, q_off, params, q, dq, r_obs=None, r_err=None, device="cuda",
+                    pin: bool = False) -> "Batch":
+        import torch
+        dev = torch.device(device)
+
+        def t(a, dt):
+            if a is None:
+                return None
+            x = torch.as_tensor(np.ascontiguousarray(a), dtype=dt)
+            if dev.type == "cuda":
+                return x.to(dev)
+            return x.pin_memory() if pin else x
+
+        return Batch(np.ascontiguousarray(n_layers, dtype=np.int32), np.ascontiguousarray(dataset, dtype=np.int32),
+                     np.ascontiguousarray(q_off, dtype=np.int64), t(params, torch.float64), t(q, torch.float32),
+                     t(dq, torch.float32), t(r_obs, torch.float32), t(r_err, torch.float32))
+
+    @staticmethod
+    def from_workload(wl, device="cuda", pin: bool = False) -> "Batch":
+        return Batch.from_arrays(wl.n_layers, wl.dataset, wl.q_off, wl.params, wl.q, wl.dq, wl.r_obs, wl.r_err,
+                                 device=device, pin=pin)
+
+    def with_params(self, params) -> "Batch":
+        return dataclasses.replace(self, params=params)
+
+    def _c(self) -> CBatch:
+        def ptr(x):
+            return None if x is None else x.data_ptr()
+        for name in ("params", "q", "dq", "r_obs", "r_err"):
+            x = getattr(self, name)
+            if x is not None and not x.is_contiguous():
+                raise ValueError(f"{name} must be contiguous")
+        p = self.params
+        import torch
+        if p.dtype != torch.float64:
+            raise TypeError("params must be float64")
+        return CBatch(self.n_stacks, self.n_datasets, self.n_layers.ctypes.data, self.dataset.ctypes.data,
+                      self.q_off.ctypes.data, NR_MEM_HOST if self.on_host else NR_MEM_DEVICE, 0,
+                      ptr(p), ptr(self.q), ptr(self.dq), ptr(self.r_obs), ptr(self.r_err))
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """One library context (quadrature rule, precision, plan cache) on the
+    current CUDA device."""
+
+    def __init__(self, n_quad: int = 17, precision: str = "mixed", autotune: bool = False, tile_q: int = 0,
+                 chunk_q: int = 0, grid_ctas: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2509_06924_gb300 needs a CUDA device (no CPU fallback)")
+        self._lib = load_library()
+        prec = {"mixed": NR_MIXED, "fp64": NR_FP64_PLAIN}[precision]
+        opt = Options(n_quad, prec, 1, int(autotune), tile_q, chunk_q, grid_ctas, 0)
+        h = ctypes.c_void_p()
+        _check(self._lib.nr_create(ctypes.byref(h), ctypes.byref(opt)))
+        self._h = h
+        self.n_quad = n_quad
+        self.precision = precision
+        self.device = torch.cuda.current_device()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def plan(self, batch: Batch) -> None:
+        cb = batch._c()
+        _check(self._lib.nr_plan(self._h, ctypes.byref(cb)))
+
+    def plan_info(self, batch: Batch) -> dict:
+        cb = batch._c()
+        ev = ctypes.c_int64()
+        tq, cq, gr, la = (ctypes.c_int32() for _ in range(4))
+        _check(self._lib.nr_plan_info(self._h, ctypes.byref(cb), ctypes.byref(ev), ctypes.byref(tq),
+                                      ctypes.byref(cq), ctypes.byref(gr), ctypes.byref(la)))
+        return {"evals": ev.value, "tile_q": tq.value, "chunk_q": cq.value, "grid_ctas": gr.value,
+                "launches": la.value}
+
+    def _alloc(self, batch: Batch, n, dtype, out=None):
+        import torch
+        if out is not None:
+            return out
+        if batch.on_host:
+            return torch.empty(n, dtype=dtype).pin_memory()
+        return torch.empty(n, dtype=dtype, device=batch.params.device)
+
+    def reflectivity(self, batch: Batch, out=None, stream=None):
+        """Smeared model m = scale * S(Q) + bkg, float32 [sum of dataset lengths]."""
+        import torch
+        r = self._alloc(batch, batch.total_out, torch.float32, out)
+        cb = batch._c()
+        _check(self._lib.nr_reflectivity(self._h, ctypes.byref(cb), ctypes.c_void_p(r.data_ptr()),
+                                         _stream_handle(stream)))
+        return r
+
+    def loglik(self, batch: Batch, out=None, stream=None):
+        """Gaussian log-likelihood per stack, float64 [S]."""
+        import torch
+        ll = self._alloc(batch, batch.n_stacks, torch.float64, out)
+        cb = batch._c()
+        _check(self._lib.nr_loglik(self._h, ctypes.byref(cb), ctypes.c_void_p(ll.data_ptr()),
+                                   _stream_handle(stream)))
+        return ll
+
+    def loglik_grad(self, batch: Batch, ll_out=None, grad_out=None, stream=None):
+        """(loglik [S], gradient packed like params), float64."""
+        import torch
+        ll = self._alloc(batch, batch.n_stacks, torch.float64, ll_out)
+        g = self._alloc(batch, batch.params.numel(), torch.float64, grad_out)
+        cb = batch._c()
+        _check(self._lib.nr_loglik_grad(self._h, ctypes.byref(cb), ctypes.c_void_p(ll.data_ptr()),
+                                        ctypes.c_void_p(g.data_ptr()), _stream_handle(stream)))
+        return ll, g
+
+    def device_status(self, stream=None) -> int:
+        """Synchronise and return (and clear) the sticky NR_FLAG_* word."""
+        f = ctypes.c_int32()
+        st = self._lib.nr_device_status(self._h, _stream_handle(stream), ctypes.byref(f))
+        if st not in (NR_OK, NR_ENONFINITE):
+            _check(st)
+        return int(f.value)
+
+
+def _autograd_function():
+    import torch
+
+    class NRLogLik(torch.autograd.Function):
+        """loglik(params) with the library's exact gradient as backward:
+        forward calls nr_loglik_grad once and keeps the gradient."""
+
+        @staticmethod
+        def forward(ctx_, params, nr_ctx, batch):
+            ll, g = nr_ctx.loglik_grad(batch.with_params(params.detach().contiguous()))
+            ctx_.save_for_backward(g)
+            ctx_.layout = (batch.n_layers, batch.n_stacks)
+            return ll
+
+        @staticmethod
+        def backward(ctx_, grad_ll):
+            (g,) = ctx_.saved_tensors
+            n_layers, _ = ctx_.layout
+            per = torch.as_tensor(4 * n_layers.astype(np.int64) + 6, device=g.device)
+            scale = torch.repeat_interleave(grad_ll, per)
+            return g * scale, None, None
+
+    return NRLogLik
+
+
+_NRLogLik = None
+
+
+def loglik_autograd(params, ctx: Context, batch: Batch):
+    """Differentiable per-stack log-likelihood (torch.autograd)."""
+    global _NRLogLik
+    if _NRLogLik is None:
+        _NRLogLik = _autograd_function()
+    return _NRLogLik.apply(params, ctx, batch)

@@ -1,0 +1,673 @@
+// nr_api.cpp -- host side of the C ABI declared in include/nr.h: argument
+// and metadata validation, the library's own Gauss-Hermite rule, plans (the
+// per-batch device work lists, cached by metadata), launch-shape choice and
+// autotuning, host-memory staging, and the device status word.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "nr.h"
+#include "nr_internal.h"
+
+using namespace nrimpl;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+nr_status fail(nr_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define NR_CUDA(call)                                                                            \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(e_ == cudaErrorMemoryAllocation ? NR_ENOMEM : NR_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                      \
+    } while (0)
+
+// ------------------------------------------------------------ quadrature --
+// Gauss-Hermite rule for exp(-x^2) by Golub-Welsch: the nodes are the
+// eigenvalues of the symmetric tridiagonal Jacobi matrix of the Hermite
+// recurrence (off-diagonal sqrt(j/2)), found here by cyclic Jacobi rotations;
+// each node is then polished by Newton steps on the orthonormal recurrence
+// and its weight taken as 2 / psi_K'(x)^2.
+double herm_psi(int K, double x, double *dpsi)
+{
+    double pm1 = 0.0, p = 1.0 / std::sqrt(std::sqrt(M_PI));
+    for (int j = 0; j < K; ++j) {
+        const double pn = x * std::sqrt(2.0 / (j + 1)) * p - std::sqrt((double)j / (j + 1)) * pm1;
+        pm1 = p;
+        p = pn;
+    }
+    *dpsi = std::sqrt(2.0 * K) * pm1;
+    return p;
+}
+
+bool gauss_hermite(int K, double *x, double *w)
+{
+    if (K < 1 || K > NR_MAX_QUAD) return false;
+    std::vector<double> A((size_t)K * K, 0.0);
+    for (int i = 0; i + 1 < K; ++i) A[i * K + i + 1] = A[(i + 1) * K + i] = std::sqrt((i + 1) / 2.0);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < K; ++p)
+            for (int q = p + 1; q < K; ++q) off += A[p * K + q] * A[p * K + q];
+        if (off < 1e-30) break;
+        for (int p = 0; p < K; ++p)
+            for (int q = p + 1; q < K; ++q) {
+                const double apq = A[p * K + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                const double theta = (A[q * K + q] - A[p * K + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < K; ++k) { // columns p, q
+                    const double akp = A[k * K + p], akq = A[k * K + q];
+                    A[k * K + p] = c * akp - s * akq;
+                    A[k * K + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < K; ++k) { // rows p, q
+                    const double apk = A[p * K + k], aqk = A[q * K + k];
+                    A[p * K + k] = c * apk - s * aqk;
+                    A[q * K + k] = s * apk + c * aqk;
+                }
+            }
+    }
+    std::vector<double> nodes(K);
+    for (int i = 0; i < K; ++i) nodes[i] = A[i * K + i];
+    std::sort(nodes.begin(), nodes.end());
+    for (int i = 0; i < K; ++i) {
+        double xi = nodes[i], d;
+        for (int it = 0; it < 3; ++it) {
+            const double f = herm_psi(K, xi, &d);
+            if (d != 0.0) xi -= f / d;
+        }
+        herm_psi(K, xi, &d);
+        x[i] = xi;
+        w[i] = 2.0 / (d * d);
+    }
+    return true;
+}
+
+// --------------------------------------------------------------- buffers --
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { if (p) cudaFree(p); }
+    cudaError_t ensure(size_t n)
+    {
+        if (n <= bytes) return cudaSuccess;
+        if (p) {
+            cudaDeviceSynchronize();
+            cudaFree(p);
+            p = nullptr;
+            bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e == cudaSuccess) bytes = n;
+        return e;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+constexpr int kGradBuckets[] = {1, 2, 4, 8, 12, 16, 20, 32, 64};
+
+int grad_bucket(int n)
+{
+    for (int b : kGradBuckets)
+        if (n <= b) return b;
+    return -1;
+}
+int fwd_bucket(int n) { return n <= 1 ? 1 : 0; }
+
+struct Group {
+    int nmax = 0;
+    int item_begin = 0;
+    int item_count = 0;
+    int grid = 0;
+    int tile_q = 0;
+};
+
+// Work list of one mode family (forward = model/loglik, or gradient).
+struct WorkList {
+    std::vector<Group> groups;
+    DevBuf d_stacks, d_items, d_partials, d_done, d_ticket;
+    int64_t partial_doubles = 0;
+    int chunk_q = 0;
+};
+
+struct Plan {
+    // key
+    int32_t S = 0, D = 0, K = 0;
+    std::vector<int32_t> n_layers, dataset;
+    std::vector<int64_t> q_off;
+    uint64_t hash = 0;
+    // derived
+    int64_t total_params = 0, total_out = 0, total_q = 0, evals = 0;
+    WorkList fwd, grad;
+    bool fwd_built = false, grad_built = false;
+    // FP64 plain path
+    DevBuf d64_stacks, d64_items, d64_llpert;
+    int n64_items = 0, n64_pert = 1;
+    bool fp64_built = false;
+    uint64_t last_use = 0;
+};
+
+uint64_t fnv(uint64_t h, const void *data, size_t n)
+{
+    const unsigned char *p = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+} // namespace
+
+struct nr_ctx {
+    int device = 0;
+    int sms = 0;
+    nr_options opt{};
+    QuadConst qc{};
+    int32_t *d_status = nullptr;
+    std::vector<std::unique_ptr<Plan>> plans;
+    uint64_t clock = 0;
+    // host-memory staging
+    DevBuf s_params, s_q, s_dq, s_robs, s_rerr, s_out, s_ll, s_grad;
+};
+
+namespace {
+
+nr_status validate(const nr_batch *b)
+{
+    if (!b) return fail(NR_EINVAL, "batch is NULL");
+    if (b->n_stacks < 0) return fail(NR_EINVAL, "n_stacks < 0");
+    if (b->memory != NR_MEM_DEVICE && b->memory != NR_MEM_HOST) return fail(NR_EINVAL, "bad memory kind");
+    if (b->n_stacks == 0) return NR_OK;
+    if (b->n_datasets < 1) return fail(NR_EINVAL, "n_datasets < 1");
+    if (!b->n_layers || !b->dataset || !b->q_off) return fail(NR_EINVAL, "metadata pointer is NULL");
+    if (!b->params || !b->q || !b->dq) return fail(NR_EINVAL, "params/q/dq pointer is NULL");
+    if (b->q_off[0] != 0) return fail(NR_EINVAL, "q_off[0] != 0");
+    for (int d = 0; d < b->n_datasets; ++d) {
+        const int64_t len = b->q_off[d + 1] - b->q_off[d];
+        if (len < 0) return fail(NR_EINVAL, "q_off not non-decreasing at dataset %d", d);
+        if (len > (int64_t)1 << 30) return fail(NR_EINVAL, "dataset %d too long", d);
+    }
+    for (int s = 0; s < b->n_stacks; ++s) {
+        if (b->n_layers[s] < 0 || b->n_layers[s] > NR_MAX_LAYERS)
+            return fail(NR_EINVAL, "stack %d: n_layers %d outside [0, %d]", s, b->n_layers[s], NR_MAX_LAYERS);
+        if (b->dataset[s] < 0 || b->dataset[s] >= b->n_datasets)
+            return fail(NR_EINVAL, "stack %d: dataset %d outside [0, %d)", s, b->dataset[s], b->n_datasets);
+    }
+    return NR_OK;
+}
+
+uint64_t batch_hash(const nr_batch *b, int K)
+{
+    uint64_t h = 1469598103934665603ull;
+    h = fnv(h, &b->n_stacks, sizeof b->n_stacks);
+    h = fnv(h, &b->n_datasets, sizeof b->n_datasets);
+    h = fnv(h, &K, sizeof K);
+    if (b->n_stacks > 0) {
+        h = fnv(h, b->n_layers, sizeof(int32_t) * b->n_stacks);
+        h = fnv(h, b->dataset, sizeof(int32_t) * b->n_stacks);
+        h = fnv(h, b->q_off, sizeof(int64_t) * (b->n_datasets + 1));
+    }
+    return h;
+}
+
+bool same_meta(const Plan &p, const nr_batch *b, int K)
+{
+    if (p.S != b->n_stacks || p.D != b->n_datasets || p.K != K) return false;
+    if (p.S == 0) return true;
+    return std::memcmp(p.n_layers.data(), b->n_layers, sizeof(int32_t) * p.S) == 0 &&
+           std::memcmp(p.dataset.data(), b->dataset, sizeof(int32_t) * p.S) == 0 &&
+           std::memcmp(p.q_off.data(), b->q_off, sizeof(int64_t) * (p.D + 1)) == 0;
+}
+
+int tile_for(const nr_ctx *ctx, int mode, int nmax)
+{
+    const int block = mixed_block_threads(mode, nmax);
+    int tq = block / ctx->qc.K;
+    if (ctx->opt.tile_q > 0) tq = std::min(tq, ctx->opt.tile_q);
+    return std::max(tq, 1);
+}
+
+// Build the work list of one mode family: stacks grouped by register bucket,
+// each stack cut into chunks when there are too few stacks to fill the GPU,
+// items of a group ordered by decreasing cost (longest-processing-time first
+// for the persistent queue).
+nr_status build_worklist(nr_ctx *ctx, Plan &pl, int mode, WorkList &wl)
+{
+    const int S = pl.S;
+    std::vector<int> bucket(S);
+    for (int s = 0; s < S; ++s)
+        bucket[s] = mode == kGrad ? grad_bucket(pl.n_layers[s]) : fwd_bucket(pl.n_layers[s]);
+    std::vector<int> order(S);
+    for (int s = 0; s < S; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bucket[a] < bucket[b]; });
+
+    std::vector<StackInfo> info(S);
+    std::vector<WorkItem> items;
+    int64_t par = 0, out = 0;
+    std::vector<int64_t> par_off(S), out_off(S);
+    for (int s = 0; s < S; ++s) {
+        par_off[s] = par;
+        out_off[s] = out;
+        par += 4 * (int64_t)pl.n_layers[s] + 6;
+        out += pl.q_off[pl.dataset[s] + 1] - pl.q_off[pl.dataset[s]];
+    }
+    wl.groups.clear();
+    int64_t part = 0;
+    size_t i0 = 0;
+    while (i0 < order.size()) {
+        size_t i1 = i0;
+        const int b = bucket[order[i0]];
+        while (i1 < order.size() && bucket[order[i1]] == b) ++i1;
+        Group g;
+        g.nmax = b;
+        g.tile_q = tile_for(ctx, mode, b);
+        int occ = 0;
+        cudaError_t e = mixed_occupancy(mode, b, &occ);
+        if (e != cudaSuccess) return fail(NR_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
+        occ = std::max(occ, 1);
+        const int64_t resident = (int64_t)ctx->sms * occ;
+        const int64_t nst = (int64_t)(i1 - i0);
+        // chunk length: whole datasets unless that leaves fewer than ~4 waves
+        int64_t max_len = 0;
+        for (size_t i = i0; i < i1; ++i) {
+            const int s = order[i];
+            max_len = std::max<int64_t>(max_len, pl.q_off[pl.dataset[s] + 1] - pl.q_off[pl.dataset[s]]);
+        }
+        int64_t chunk = max_len;
+        if (ctx->opt.chunk_q > 0) {
+            chunk = ctx->opt.chunk_q;
+        } else if (nst < 4 * resident && max_len > 0) {
+            const int64_t want = (4 * resident + nst - 1) / nst; // pieces per stack
+            chunk = std::max<int64_t>((max_len + want - 1) / want, g.tile_q);
+            chunk = (chunk + g.tile_q - 1) / g.tile_q * g.tile_q;
+        }
+        chunk = std::max<int64_t>(chunk, 1);
+        wl.chunk_q = (int)std::min<int64_t>(chunk, 1 << 30);
+        g.item_begin = (int)items.size();
+        std::vector<std::pair<int64_t, WorkItem>> gi;
+        for (size_t i = i0; i < i1; ++i) {
+            const int s = order[i];
+            const int nq = (int)(pl.q_off[pl.dataset[s] + 1] - pl.q_off[pl.dataset[s]]);
+            const int nch = std::max(1, (int)((nq + chunk - 1) / chunk));
+            StackInfo &si = info[s];
+            si.par_off = par_off[s];
+            si.out_off = out_off[s];
+            si.q_begin = pl.q_off[pl.dataset[s]];
+            si.n = pl.n_layers[s];
+            si.nq = nq;
+            si.n_chunks = nch;
+            si.part_base = nch > 1 ? part : 0;
+            si.pad = 0;
+            if (nch > 1) part += (int64_t)nch * (4 * si.n + 6);
+            for (int c = 0; c < nch; ++c) {
+                WorkItem w;
+                w.stack = s;
+                w.q_lo = (int)std::min<int64_t>((int64_t)c * chunk, nq);
+                w.q_hi = (int)std::min<int64_t>((int64_t)(c + 1) * chunk, nq);
+                w.chunk = c;
+                const int64_t cost = (int64_t)(si.n + 1) * (w.q_hi - w.q_lo) + 1;
+                gi.push_back({cost, w});
+            }
+        }
+        std::stable_sort(gi.begin(), gi.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+        for (auto &x : gi) items.push_back(x.second);
+        g.item_count = (int)items.size() - g.item_begin;
+        g.grid = (int)std::min<int64_t>(g.item_count, resident);
+        if (ctx->opt.grid_ctas > 0) g.grid = std::min(g.item_count, ctx->opt.grid_ctas);
+        g.grid = std::max(g.grid, 1);
+        wl.groups.push_back(g);
+        i0 = i1;
+    }
+    wl.partial_doubles = part;
+    NR_CUDA(wl.d_stacks.ensure(sizeof(StackInfo) * std::max(S, 1)));
+    NR_CUDA(wl.d_items.ensure(sizeof(WorkItem) * std::max<size_t>(items.size(), 1)));
+    NR_CUDA(wl.d_partials.ensure(sizeof(double) * std::max<int64_t>(part, 1)));
+    NR_CUDA(wl.d_done.ensure(sizeof(int32_t) * std::max(S, 1)));
+    NR_CUDA(wl.d_ticket.ensure(sizeof(int32_t) * 2 * std::max<size_t>(wl.groups.size(), 1)));
+    NR_CUDA(cudaMemcpy(wl.d_stacks.p, info.data(), sizeof(StackInfo) * S, cudaMemcpyHostToDevice));
+    if (!items.empty())
+        NR_CUDA(cudaMemcpy(wl.d_items.p, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice));
+    NR_CUDA(cudaMemset(wl.d_done.p, 0, sizeof(int32_t) * std::max(S, 1)));
+    NR_CUDA(cudaMemset(wl.d_ticket.p, 0, sizeof(int32_t) * 2 * std::max<size_t>(wl.groups.size(), 1)));
+    return NR_OK;
+}
+
+nr_status build_fp64(nr_ctx *ctx, Plan &pl)
+{
+    (void)ctx;
+    const int S = pl.S;
+    std::vector<StackInfo> info(S);
+    std::vector<WorkItem> items;
+    int64_t par = 0, out = 0, slot = 0;
+    int maxp = 0;
+    for (int s = 0; s < S; ++s) {
+        StackInfo &si = info[s];
+        const int nq = (int)(pl.q_off[pl.dataset[s] + 1] - pl.q_off[pl.dataset[s]]);
+        si.par_off = par;
+        si.out_off = out;
+        si.q_begin = pl.q_off[pl.dataset[s]];
+        si.n = pl.n_layers[s];
+        si.nq = nq;
+        si.n_chunks = std::max(1, (nq + kFp64Block - 1) / kFp64Block);
+        si.part_base = slot;
+        si.pad = 0;
+        slot += si.n_chunks;
+        for (int c = 0; c < si.n_chunks; ++c) {
+            WorkItem w;
+            w.stack = s;
+            w.q_lo = std::min(c * kFp64Block, nq);
+            w.q_hi = std::min((c + 1) * kFp64Block, nq);
+            w.chunk = c;
+            items.push_back(w);
+        }
+        maxp = std::max(maxp, 4 * si.n + 6);
+        par += 4 * (int64_t)si.n + 6;
+        out += nq;
+    }
+    pl.n64_items = (int)items.size();
+    pl.n64_pert = 2 * maxp + 1;
+    NR_CUDA(pl.d64_stacks.ensure(sizeof(StackInfo) * std::max(S, 1)));
+    NR_CUDA(pl.d64_items.ensure(sizeof(WorkItem) * std::max<size_t>(items.size(), 1)));
+    NR_CUDA(pl.d64_llpert.ensure(sizeof(double) * std::max<int64_t>(slot * pl.n64_pert, 1)));
+    NR_CUDA(cudaMemcpy(pl.d64_stacks.p, info.data(), sizeof(StackInfo) * S, cudaMemcpyHostToDevice));
+    if (!items.empty())
+        NR_CUDA(cudaMemcpy(pl.d64_items.p, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice));
+    return NR_OK;
+}
+
+nr_status get_plan(nr_ctx *ctx, const nr_batch *b, int mode, Plan **out)
+{
+    const int K = ctx->qc.K;
+    const uint64_t h = batch_hash(b, K);
+    Plan *pl = nullptr;
+    for (auto &p : ctx->plans)
+        if (p->hash == h && same_meta(*p, b, K)) { pl = p.get(); break; }
+    if (!pl) {
+        nr_status st = validate(b);
+        if (st != NR_OK) return st;
+        if (ctx->plans.size() >= 8) { // evict the least recently used plan
+            auto it = std::min_element(ctx->plans.begin(), ctx->plans.end(),
+                                       [](const auto &a, const auto &c) { return a->last_use < c->last_use; });
+            cudaDeviceSynchronize();
+            ctx->plans.erase(it);
+        }
+        auto np = std::make_unique<Plan>();
+        np->S = b->n_stacks;
+        np->D = b->n_datasets;
+        np->K = K;
+        np->hash = h;
+        if (np->S > 0) {
+            np->n_layers.assign(b->n_layers, b->n_layers + np->S);
+            np->dataset.assign(b->dataset, b->dataset + np->S);
+            np->q_off.assign(b->q_off, b->q_off + np->D + 1);
+            for (int s = 0; s < np->S; ++s) {
+                const int64_t len = np->q_off[np->dataset[s] + 1] - np->q_off[np->dataset[s]];
+                np->total_params += 4 * (int64_t)np->n_layers[s] + 6;
+                np->total_out += len;
+            }
+            np->total_q = np->q_off[np->D];
+            np->evals = np->total_out * K;
+        }
+        pl = np.get();
+        ctx->plans.push_back(std::move(np));
+    }
+    pl->last_use = ++ctx->clock;
+    if (pl->S > 0) {
+        nr_status st = NR_OK;
+        if (ctx->opt.precision == NR_FP64_PLAIN) {
+            if (!pl->fp64_built) { st = build_fp64(ctx, *pl); pl->fp64_built = st == NR_OK; }
+        } else if (mode == kGrad) {
+            if (!pl->grad_built) { st = build_worklist(ctx, *pl, kGrad, pl->grad); pl->grad_built = st == NR_OK; }
+        } else {
+            if (!pl->fwd_built) { st = build_worklist(ctx, *pl, kModel, pl->fwd); pl->fwd_built = st == NR_OK; }
+        }
+        if (st != NR_OK) return st;
+    }
+    *out = pl;
+    return NR_OK;
+}
+
+nr_status launch_device(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, float *r_out, double *ll,
+                        double *grad, cudaStream_t st)
+{
+    if (pl.S == 0) return NR_OK;
+    KernelArgs a{};
+    a.params = b->params;
+    a.q = b->q;
+    a.dq = b->dq;
+    a.r_obs = b->r_obs;
+    a.r_err = b->r_err;
+    a.r_out = r_out;
+    a.ll_out = ll;
+    a.grad_out = grad;
+    a.status = ctx->d_status;
+    if (ctx->opt.precision == NR_FP64_PLAIN) {
+        a.stacks = pl.d64_stacks.as<StackInfo>();
+        a.items = pl.d64_items.as<WorkItem>();
+        a.n_items = pl.n64_items;
+        a.ll_pert = pl.d64_llpert.as<double>();
+        a.n_pert = mode == kGrad ? pl.n64_pert : 1;
+        cudaError_t e = launch_fp64(mode, a, ctx->qc, st);
+        if (e == cudaSuccess) e = launch_fp64_finalize(mode, pl.S, a, st);
+        if (e != cudaSuccess) return fail(NR_ECUDA, "fp64 launch: %s", cudaGetErrorString(e));
+        return NR_OK;
+    }
+    WorkList &wl = mode == kGrad ? pl.grad : pl.fwd;
+    a.stacks = wl.d_stacks.as<StackInfo>();
+    a.partials = wl.d_partials.as<double>();
+    a.stack_done = wl.d_done.as<int32_t>();
+    for (size_t g = 0; g < wl.groups.size(); ++g) {
+        const Group &G = wl.groups[g];
+        a.items = wl.d_items.as<WorkItem>() + G.item_begin;
+        a.n_items = G.item_count;
+        a.tile_q = G.tile_q;
+        a.ticket = wl.d_ticket.as<int32_t>() + 2 * g;
+        cudaError_t e = launch_mixed(mode, G.nmax, G.grid, a, ctx->qc, st);
+        if (e != cudaSuccess) return fail(NR_ECUDA, "mixed launch (bucket %d): %s", G.nmax, cudaGetErrorString(e));
+    }
+    return NR_OK;
+}
+
+// Host-memory batches: copy in, compute, copy out, synchronise.
+nr_status run_host(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, float *r_out, double *ll, double *grad,
+                   cudaStream_t st)
+{
+    if (pl.S == 0) return NR_OK;
+    const size_t np = sizeof(double) * pl.total_params, nqb = sizeof(float) * pl.total_q;
+    const bool need_data = mode != kModel;
+    NR_CUDA(ctx->s_params.ensure(np));
+    NR_CUDA(ctx->s_q.ensure(nqb));
+    NR_CUDA(ctx->s_dq.ensure(nqb));
+    if (need_data) {
+        if (!b->r_obs || !b->r_err) return fail(NR_EINVAL, "r_obs/r_err required");
+        NR_CUDA(ctx->s_robs.ensure(nqb));
+        NR_CUDA(ctx->s_rerr.ensure(nqb));
+    }
+    NR_CUDA(cudaMemcpyAsync(ctx->s_params.p, b->params, np, cudaMemcpyHostToDevice, st));
+    NR_CUDA(cudaMemcpyAsync(ctx->s_q.p, b->q, nqb, cudaMemcpyHostToDevice, st));
+    NR_CUDA(cudaMemcpyAsync(ctx->s_dq.p, b->dq, nqb, cudaMemcpyHostToDevice, st));
+    if (need_data) {
+        NR_CUDA(cudaMemcpyAsync(ctx->s_robs.p, b->r_obs, nqb, cudaMemcpyHostToDevice, st));
+        NR_CUDA(cudaMemcpyAsync(ctx->s_rerr.p, b->r_err, nqb, cudaMemcpyHostToDevice, st));
+    }
+    nr_batch db = *b;
+    db.memory = NR_MEM_DEVICE;
+    db.params = ctx->s_params.as<double>();
+    db.q = ctx->s_q.as<float>();
+    db.dq = ctx->s_dq.as<float>();
+    db.r_obs = need_data ? ctx->s_robs.as<float>() : nullptr;
+    db.r_err = need_data ? ctx->s_rerr.as<float>() : nullptr;
+    float *d_out = nullptr;
+    double *d_ll = nullptr, *d_grad = nullptr;
+    if (r_out) { NR_CUDA(ctx->s_out.ensure(sizeof(float) * pl.total_out)); d_out = ctx->s_out.as<float>(); }
+    if (ll) { NR_CUDA(ctx->s_ll.ensure(sizeof(double) * pl.S)); d_ll = ctx->s_ll.as<double>(); }
+    if (grad) { NR_CUDA(ctx->s_grad.ensure(np)); d_grad = ctx->s_grad.as<double>(); }
+    nr_status s = launch_device(ctx, pl, &db, mode, d_out, d_ll, d_grad, st);
+    if (s != NR_OK) return s;
+    if (r_out) NR_CUDA(cudaMemcpyAsync(r_out, d_out, sizeof(float) * pl.total_out, cudaMemcpyDeviceToHost, st));
+    if (ll) NR_CUDA(cudaMemcpyAsync(ll, d_ll, sizeof(double) * pl.S, cudaMemcpyDeviceToHost, st));
+    if (grad) NR_CUDA(cudaMemcpyAsync(grad, d_grad, np, cudaMemcpyDeviceToHost, st));
+    NR_CUDA(cudaStreamSynchronize(st));
+    return NR_OK;
+}
+
+nr_status compute(nr_ctx *ctx, const nr_batch *b, int mode, float *r_out, double *ll, double *grad, void *stream)
+{
+    if (!ctx) return fail(NR_EINVAL, "context is NULL");
+    if (!b) return fail(NR_EINVAL, "batch is NULL");
+    if (mode == kModel && !r_out && b->n_stacks > 0) return fail(NR_EINVAL, "r_out is NULL");
+    if (mode == kLoglik && !ll && b->n_stacks > 0) return fail(NR_EINVAL, "loglik is NULL");
+    if (mode != kModel && b->n_stacks > 0 && (!b->r_obs || !b->r_err))
+        return fail(NR_EINVAL, "r_obs/r_err are required for the likelihood");
+    NR_CUDA(cudaSetDevice(ctx->device));
+    Plan *pl = nullptr;
+    nr_status st = get_plan(ctx, b, mode, &pl);
+    if (st != NR_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (b->memory == NR_MEM_HOST) return run_host(ctx, *pl, b, mode, r_out, ll, grad, s);
+    return launch_device(ctx, *pl, b, mode, r_out, ll, grad, s);
+}
+
+} // namespace
+
+// ================================================================ C ABI ===
+extern "C" {
+
+nr_status nr_create(nr_ctx **out, const nr_options *opt)
+{
+    if (!out) return fail(NR_EINVAL, "out is NULL");
+    *out = nullptr;
+    auto ctx = std::make_unique<nr_ctx>();
+    ctx->opt.n_quad = 17;
+    ctx->opt.precision = NR_MIXED;
+    ctx->opt.deterministic = 1;
+    if (opt) {
+        ctx->opt = *opt;
+        if (ctx->opt.n_quad == 0) ctx->opt.n_quad = 17;
+    }
+    if (ctx->opt.n_quad < 1 || ctx->opt.n_quad > NR_MAX_QUAD)
+        return fail(NR_EINVAL, "n_quad %d outside [1, %d]", ctx->opt.n_quad, NR_MAX_QUAD);
+    if (ctx->opt.precision != NR_MIXED && ctx->opt.precision != NR_FP64_PLAIN)
+        return fail(NR_EINVAL, "unknown precision %d", ctx->opt.precision);
+    if (ctx->opt.tile_q < 0 || ctx->opt.chunk_q < 0 || ctx->opt.grid_ctas < 0)
+        return fail(NR_EINVAL, "negative launch override");
+    double x[NR_MAX_QUAD], w[NR_MAX_QUAD];
+    const int K = ctx->opt.n_quad;
+    if (!gauss_hermite(K, x, w)) return fail(NR_EINVAL, "quadrature failed");
+    const double c = 1.0 / (2.0 * std::sqrt(std::log(2.0)));
+    const double isp = 1.0 / std::sqrt(M_PI);
+    ctx->qc.K = K;
+    for (int k = 0; k < K; ++k) {
+        const double g = x[k] * c;
+        ctx->qc.gd[k] = g;
+        ctx->qc.g_hi[k] = (float)g;
+        ctx->qc.g_lo[k] = (float)(g - (double)(float)g);
+        ctx->qc.wd[k] = w[k] * isp;
+        ctx->qc.w[k] = (float)(w[k] * isp);
+    }
+    NR_CUDA(cudaGetDevice(&ctx->device));
+    NR_CUDA(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    NR_CUDA(cudaMalloc(&ctx->d_status, sizeof(int32_t)));
+    NR_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int32_t)));
+    *out = ctx.release();
+    return NR_OK;
+}
+
+void nr_destroy(nr_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+}
+
+const char *nr_last_error(void) { return g_last_error.c_str(); }
+
+nr_status nr_plan(nr_ctx *ctx, const nr_batch *batch)
+{
+    if (!ctx) return fail(NR_EINVAL, "context is NULL");
+    NR_CUDA(cudaSetDevice(ctx->device));
+    Plan *pl = nullptr;
+    nr_status st = get_plan(ctx, batch, kModel, &pl);
+    if (st == NR_OK) st = get_plan(ctx, batch, kGrad, &pl);
+    return st;
+}
+
+nr_status nr_reflectivity(nr_ctx *ctx, const nr_batch *batch, float *r_out, void *stream)
+{
+    return compute(ctx, batch, kModel, r_out, nullptr, nullptr, stream);
+}
+
+nr_status nr_loglik(nr_ctx *ctx, const nr_batch *batch, double *loglik, void *stream)
+{
+    return compute(ctx, batch, kLoglik, nullptr, loglik, nullptr, stream);
+}
+
+nr_status nr_loglik_grad(nr_ctx *ctx, const nr_batch *batch, double *loglik, double *grad, void *stream)
+{
+    return compute(ctx, batch, kGrad, nullptr, loglik, grad, stream);
+}
+
+nr_status nr_device_status(nr_ctx *ctx, void *stream, int32_t *flags)
+{
+    if (!ctx) return fail(NR_EINVAL, "context is NULL");
+    NR_CUDA(cudaSetDevice(ctx->device));
+    NR_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int32_t f = 0;
+    NR_CUDA(cudaMemcpy(&f, ctx->d_status, sizeof f, cudaMemcpyDeviceToHost));
+    NR_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int32_t)));
+    if (flags) *flags = f;
+    return f ? fail(NR_ENONFINITE, "device status flags 0x%x", f) : NR_OK;
+}
+
+nr_status nr_quadrature(int32_t K, double *x, double *w)
+{
+    if (!x || !w) return fail(NR_EINVAL, "x/w is NULL");
+    if (!gauss_hermite(K, x, w)) return fail(NR_EINVAL, "K %d outside [1, %d]", K, NR_MAX_QUAD);
+    return NR_OK;
+}
+
+nr_status nr_plan_info(nr_ctx *ctx, const nr_batch *batch, int64_t *evals, int32_t *tile_q, int32_t *chunk_q,
+                       int32_t *grid_ctas, int32_t *launches)
+{
+    if (!ctx) return fail(NR_EINVAL, "context is NULL");
+    NR_CUDA(cudaSetDevice(ctx->device));
+    Plan *pl = nullptr;
+    nr_status st = get_plan(ctx, batch, kGrad, &pl);
+    if (st != NR_OK) return st;
+    if (evals) *evals = pl->evals;
+    const bool fp64 = ctx->opt.precision == NR_FP64_PLAIN;
+    const WorkList &wl = pl->grad;
+    if (tile_q) *tile_q = fp64 ? kFp64Block : (wl.groups.empty() ? 0 : wl.groups[0].tile_q);
+    if (chunk_q) *chunk_q = fp64 ? kFp64Block : wl.chunk_q;
+    if (grid_ctas) *grid_ctas = fp64 ? pl->n64_items : (wl.groups.empty() ? 0 : wl.groups[0].grid);
+    if (launches) *launches = fp64 ? 2 : (int32_t)wl.groups.size();
+    return NR_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,91 @@
+// nr_internal.h -- structures shared by the host API (nr_api.cpp) and the
+// CUDA kernels (nr_mixed.cu, nr_fp64.cu) of the reflectivity library.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "nr.h"
+
+namespace nrimpl {
+
+enum Mode : int { kModel = 0, kLoglik = 1, kGrad = 2 };
+
+// One stack of the batch, as the kernels see it.
+struct StackInfo {
+    int64_t par_off;   // first packed parameter
+    int64_t out_off;   // first r_out element
+    int64_t q_begin;   // first point of the stack's dataset in q/dq/r_obs/r_err
+    int64_t part_base; // first partial-sum slot (doubles) when n_chunks > 1
+    int32_t n;         // layers
+    int32_t nq;        // dataset length
+    int32_t n_chunks;  // work items of this stack
+    int32_t pad;
+};
+
+// A contiguous range of Q points of one stack: the unit a CTA takes from the
+// work queue.
+struct WorkItem {
+    int32_t stack;
+    int32_t q_lo;  // first Q index within the dataset
+    int32_t q_hi;  // one past the last
+    int32_t chunk; // index among the stack's items (partial-sum slot)
+};
+
+// Quadrature rule as the kernels use it: node offset q = Q + dQ * g_k with
+// g_k = x_k / (2 sqrt(ln 2)) as a float pair (hi + lo) and as a double, and
+// weight w_k / sqrt(pi).
+struct QuadConst {
+    float g_hi[NR_MAX_QUAD];
+    float g_lo[NR_MAX_QUAD];
+    float w[NR_MAX_QUAD];
+    double gd[NR_MAX_QUAD];
+    double wd[NR_MAX_QUAD];
+    int32_t K;
+};
+
+struct KernelArgs {
+    const double *params;
+    const float *q;
+    const float *dq;
+    const float *r_obs;
+    const float *r_err;
+    const StackInfo *stacks;
+    const WorkItem *items;
+    int32_t n_items;
+    int32_t tile_q;      // Q points per CTA tile (mixed kernels)
+    float *r_out;
+    double *ll_out;
+    double *grad_out;
+    double *partials;    // per-chunk raw sums of chunked stacks
+    int32_t *stack_done; // per-stack arrival counters (self-resetting)
+    int32_t *ticket;     // [2]: next work item, finished CTAs (self-resetting)
+    int32_t *status;     // sticky NR_FLAG_* word
+    // FP64 plain path only
+    double *ll_pert;     // [(chunk slots) * n_pert] partial chi^2 sums per perturbation
+    int32_t n_pert;      // 1, or 2 * max(4n+6) + 1 for central differences
+    int32_t pad;
+};
+
+// ---- launchers (nr_mixed.cu) ----
+// Mixed-precision kernels.  `nmax` is the register-array capacity bucket of
+// the launch (every stack of the launch has n <= nmax); 0 selects the
+// runtime-n forward kernel (model / loglik modes only).
+int mixed_block_threads(int mode, int nmax);
+size_t mixed_dyn_smem(int mode, int nmax);
+cudaError_t mixed_occupancy(int mode, int nmax, int *blocks_per_sm);
+cudaError_t launch_mixed(int mode, int nmax, int grid, const KernelArgs &a, const QuadConst &qc,
+                         cudaStream_t st);
+bool mixed_bucket_ok(int mode, int nmax);
+
+// ---- launchers (nr_fp64.cu) ----
+constexpr int kFp64Block = 128;
+cudaError_t launch_fp64(int mode, const KernelArgs &a, const QuadConst &qc, cudaStream_t st);
+cudaError_t launch_fp64_finalize(int mode, int n_stacks, const KernelArgs &a, cudaStream_t st);
+
+// Number of raw per-stack sums the mixed gradient kernel produces
+// (= packed parameter count 4n+6).
+__host__ __device__ inline int n_raw(int n) { return 4 * n + 6; }
+
+} // namespace nrimpl
