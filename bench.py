@@ -73,6 +73,25 @@ def _dist():
     return ws, rank, local
 
 
+def rank_workload(name: str, rank: int, n_stacks=None):
+    """Weak scaling: every rank evaluates its own seeded copy of the workload
+    (independent parameter samples, same datasets); no data moves between
+    ranks."""
+    from paper_2509_06924_gb300 import workloads as W
+    return W.make_workload(name, n_stacks=n_stacks, seed_offset=rank)
+
+
+def max_over_ranks(value: float, device) -> float:
+    """The slowest rank's time (the only collective: a scalar all-reduce)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
 
@@ -226,7 +245,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    wl = W.make_workload(args.workload, n_stacks=args.stacks, seed_offset=rank)
+    wl = rank_workload(args.workload, rank, args.stacks)
     ctx = nr.Context(n_quad=wl.n_quad)
     batch = nr.Batch.from_workload(wl, device=dev)
     ctx.plan(batch)
@@ -263,10 +282,7 @@ def run_ours(args):
         dist.barrier()
     per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = sum(per_step) / len(per_step)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     evals = wl.evals
     value = ws * evals / (ms * 1e-3)
 

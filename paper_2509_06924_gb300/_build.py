@@ -50,23 +50,27 @@ def _run(cmd):
     return r
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if needed) and return the path of libnr.so."""
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, defines=None, out: str | None = None) -> str:
+    """Compile (if needed) and return the path of libnr.so.  `defines`
+    (e.g. {"NR_MINB_GRAD1": 3}) and `out` build a variant library elsewhere."""
+    lib_path = out or LIB
+    if not force and out is None and not _stale():
         return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    out_dir = os.path.dirname(lib_path)
+    os.makedirs(out_dir, exist_ok=True)
+    dflags = [f"-D{k}={v}" for k, v in (defines or {}).items()]
     nvcc = _nvcc()
     inc = ["-I", INCLUDE, "-I", CSRC]
     jobs = []
     objs = []
     for src in CU_SOURCES:
-        obj = os.path.join(OUT_DIR, src + ".o")
+        obj = os.path.join(out_dir, src + ".o")
         objs.append(obj)
-        jobs.append([nvcc, "-std=c++17", *ARCH, "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
+        jobs.append([nvcc, "-std=c++17", *ARCH, "-O3", "-lineinfo", "-Xcompiler", "-fPIC", *dflags,
                      "-Xptxas", "-v" if verbose else "-O3", *inc, "-c", os.path.join(CSRC, src), "-o", obj])
     cuda_inc = os.path.join(_cuda_home(), "include")
     for src in CPP_SOURCES:
-        obj = os.path.join(OUT_DIR, src + ".o")
+        obj = os.path.join(out_dir, src + ".o")
         objs.append(obj)
         jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", *inc, "-I", cuda_inc, "-c",
                      os.path.join(CSRC, src), "-o", obj])
@@ -75,10 +79,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if verbose:
         for r in results:
             print(r.stdout + r.stderr)
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -12,6 +12,10 @@ namespace nrimpl {
 
 enum Mode : int { kModel = 0, kLoglik = 1, kGrad = 2 };
 
+// Lanes that share one Q point's smearing sum in the mixed kernels; a tile
+// therefore holds at most (threads per CTA) / kSubLanes Q points.
+constexpr int kSubLanes = 4;
+
 // One stack of the batch, as the kernels see it.
 struct StackInfo {
     int64_t par_off;   // first packed parameter

@@ -41,7 +41,19 @@ constexpr float kTwoPiLo = -1.74845553146951715e-07f;    // 2 pi - kTwoPiHi
 constexpr double kFourPiD = 12.566370614359172953850573533118;
 constexpr float kLog2Pi = 1.83787706640934548356f;       // ln(2 pi)
 // |k_j|^2 < kEdgeFrac k_0^2 selects the interior-edge guard of the adjoint
-constexpr float kEdgeFrac = 0.04f;
+#ifndef NR_EDGE_FRAC
+#define NR_EDGE_FRAC 0.04f
+#endif
+constexpr float kEdgeFrac = NR_EDGE_FRAC;
+
+// CTAs per SM the compiler is asked to fit (register cap) for the 1-layer
+// gradient bucket and the forward kernels; overridable at build time.
+#ifndef NR_MINB_GRAD1
+#define NR_MINB_GRAD1 4
+#endif
+#ifndef NR_MINB_FWD
+#define NR_MINB_FWD 4
+#endif
 
 // ------------------------------------------------------------ primitives --
 __device__ __forceinline__ float rcp_approx(float x)
@@ -242,7 +254,8 @@ __device__ __forceinline__ Hyp hyp_scaled(float2 x, float m)
     return h;
 }
 
-__device__ __noinline__ float2 edge_ubar(float2 a, float2 k, float2 b, float s1, float s2, float d, float2 Z,
+template <bool INL>
+__device__ float2 edge_ubar_impl(float2 a, float2 k, float2 b, float s1, float s2, float d, float2 Z,
                                          float2 Xbar_up)
 {
     const float2 u = csqr(k);
@@ -284,6 +297,16 @@ __device__ __noinline__ float2 edge_ubar(float2 a, float2 k, float2 b, float s1,
     const float2 dXdu = cdiv(csub(dxn, cmul(X, dden)), den);
     return cmulc(dXdu, Xbar_up);
 }
+__device__ __noinline__ float2 edge_ubar_call(float2 a, float2 k, float2 b, float s1, float s2, float d, float2 Z,
+                                              float2 Xbar_up)
+{
+    return edge_ubar_impl<false>(a, k, b, s1, s2, d, Z, Xbar_up);
+}
+__device__ __forceinline__ float2 edge_ubar_inline(float2 a, float2 k, float2 b, float s1, float s2, float d,
+                                                   float2 Z, float2 Xbar_up)
+{
+    return edge_ubar_impl<true>(a, k, b, s1, s2, d, Z, Xbar_up);
+}
 
 // --------------------------------------------------------------- traits ---
 template <int MODE, int NMAX>
@@ -299,8 +322,11 @@ struct Traits {
     static constexpr int NACC = kGradMode ? 4 * NM + 3 : 0;   // partial gradients per thread
     static constexpr int NRAW = 4 * NM + 6;
     static constexpr int WARPS = BLOCK / 32;
+    // the 1-layer bucket runs the interior-edge guard after the adjoint sweep
+    // (inlined, little else live); deeper buckets call it in the sweep
+    static constexpr bool EDGE_DEFER = kGradMode && NMAX == 1;
     // shallow gradient buckets: cap registers so that 4 CTAs fit on an SM
-    static constexpr int MINB = !kGradMode ? 4 : NMAX == 1 ? 4 : NMAX <= 4 ? 3 : NMAX <= 20 ? 2 : 4;
+    static constexpr int MINB = !kGradMode ? NR_MINB_FWD : NMAX == 1 ? NR_MINB_GRAD1 : NMAX <= 20 ? 2 : 4;
 };
 
 // Per-stack parameters staged in shared memory.
@@ -395,8 +421,6 @@ __device__ void finalize_stack(const double *raw, int n, const double *p, int s,
 }
 
 // ---------------------------------------------------------------- kernel --
-constexpr int kSubLanes = 4; // lanes that share one Q point's smearing sum
-
 template <int MODE, int NMAX>
 __global__ void __launch_bounds__(Traits<MODE, NMAX>::BLOCK, Traits<MODE, NMAX>::MINB)
 nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
@@ -609,6 +633,9 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 Kz kjm1 = kj;                          // k_{j-1}
                 float2 Xb_up = make_float2(0.f, 0.f);  // adjoint of X_{j-1}
                 const float edge_u = kEdgeFrac * k0h * k0h;
+                // deferred guard inputs (1-layer bucket: only medium 1 can be interior)
+                bool edge_pending = false;
+                float2 e_a, e_k, e_b, e_Z, e_Xb;
                 auto adj_step = [&](int j) __attribute__((always_inline)) {
                     const float2 Xb_in = Xb;
                     float2 Zj = make_float2(0.f, 0.f);
@@ -666,10 +693,15 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         const float m2 = fmaf(kj.re, kj.re, kj.im * kj.im);
                         if (m2 < edge_u) {
                             // interior critical edge: conj(kbar)/k_j = 2 conj(ubar)
-                            const float2 ub = edge_ubar(kc(kjm1), kc(kj), kc(kj1), sm.sg[j - 1], sm.sg[j],
-                                                        sm.d[j].x, Zj, Xb_up);
-                            acc_add(oUr + j - 1, 2.f * ub.x);
-                            acc_add(oUi + j - 1, -2.f * ub.y);
+                            if constexpr (T::EDGE_DEFER) {
+                                edge_pending = true;
+                                e_a = kc(kjm1); e_k = kc(kj); e_b = kc(kj1); e_Z = Zj; e_Xb = Xb_up;
+                            } else {
+                                const float2 ub = edge_ubar_call(kc(kjm1), kc(kj), kc(kj1), sm.sg[j - 1],
+                                                                 sm.sg[j], sm.d[j].x, Zj, Xb_up);
+                                acc_add(oUr + j - 1, 2.f * ub.x);
+                                acc_add(oUi + j - 1, -2.f * ub.y);
+                            }
                         } else {
                             const float2 kk = cmul(kbar, kc(kj));
                             const float inv = m2 > 0.f ? rcp_approx(m2) : 0.f;
@@ -696,6 +728,13 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 } else {
 #pragma unroll 1
                     for (int j = 0; j <= n; ++j) adj_step(j);
+                }
+                if constexpr (T::EDGE_DEFER) {
+                    if (edge_pending) {
+                        const float2 ub = edge_ubar_inline(e_a, e_k, e_b, sm.sg[0], sm.sg[1], sm.d[1].x, e_Z, e_Xb);
+                        acc_add(oUr + 0, 2.f * ub.x);
+                        acc_add(oUi + 0, -2.f * ub.y);
+                    }
                 }
             }
             // no end-of-tile barrier: the next tile uses the other buffers

@@ -1,0 +1,149 @@
+"""CPU-only checks of the C-ABI library: it builds for sm_103a, loads, exports
+every entry point include/nr.h declares, and its host-side pieces (the
+quadrature rule, argument validation without a device) behave.  No kernel is
+launched here."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2509_06924_gb300 as nr
+from paper_2509_06924_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "nr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:nr_status|void|const char \*)\s*\*?\s*(nr_\w+)\s*\(", text, re.M)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib = nr.load_library()
+    declared = header_functions()
+    assert len(declared) >= 10, declared
+    for name in declared:
+        assert hasattr(lib, name), f"{name} declared in nr.h but not exported"
+    assert set(declared) == set(nr.EXPORTS)
+
+
+@pytest.mark.parametrize("K", list(range(1, 33)))
+def test_library_quadrature_matches_numpy(K):
+    x, w = nr.quadrature(K)
+    xr, wr = np.polynomial.hermite.hermgauss(K)
+    np.testing.assert_allclose(x, xr, rtol=0, atol=1e-12 * max(1, np.abs(xr).max()))
+    np.testing.assert_allclose(w, wr, rtol=1e-10, atol=1e-15)
+    assert abs(w.sum() - math.sqrt(math.pi)) < 1e-13
+
+
+def test_library_and_oracle_quadratures_agree():
+    # two independent constructions (Jacobi eigenvalues + Newton vs bisection
+    # + Newton; derivative vs Christoffel weights)
+    for K in (17, 21, 32):
+        x1, w1 = nr.quadrature(K)
+        x2, w2 = oracle.gauss_hermite(K)
+        np.testing.assert_allclose(x1, x2, rtol=0, atol=5e-13)
+        np.testing.assert_allclose(w1, w2, rtol=1e-11, atol=1e-16)
+
+
+def test_quadrature_rejects_bad_order():
+    lib = nr.load_library()
+    x = np.zeros(64)
+    w = np.zeros(64)
+    for K in (0, -3, nr.MAX_QUAD + 1):
+        st = lib.nr_quadrature(K, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        assert st == nr.NR_EINVAL
+        assert b"outside" in lib.nr_last_error()
+
+
+def test_null_arguments_are_rejected_without_a_device():
+    lib = nr.load_library()
+    assert lib.nr_create(None, None) == nr.NR_EINVAL
+    assert lib.nr_loglik(None, None, None, None) == nr.NR_EINVAL
+    assert lib.nr_plan(None, None) == nr.NR_EINVAL
+    lib.nr_destroy(None)  # no-op
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    lib = nr.load_library()
+    h = ctypes.c_void_p()
+    st = lib.nr_create(ctypes.byref(h), None)
+    assert st in (nr.NR_ECUDA, nr.NR_ENOMEM)
+    assert h.value is None
+    assert len(lib.nr_last_error()) > 0
+
+
+def test_context_refuses_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError):
+        nr.Context()
+
+
+def test_struct_layouts_match_header():
+    # nr_options: 8 int32; nr_batch: 2 int32, 3 pointers, 2 int32, 5 pointers
+    assert ctypes.sizeof(nr.Options) == 32
+    assert ctypes.sizeof(nr.CBatch) == 8 + 3 * 8 + 8 + 5 * 8
+
+
+# ------------------------------------------------------------- workloads ----
+def test_workloads_are_seeded_and_shaped():
+    a = W.make_workload("thick_oxide", n_stacks=10)
+    b = W.make_workload("thick_oxide", n_stacks=10)
+    np.testing.assert_array_equal(a.params, b.params)
+    assert a.n_stacks == 10 and a.n_quad == 21 and int(a.q_off[-1]) == 400
+    assert a.evals == 10 * 400 * 21
+    L = W.layout(1)
+    d = a.params.reshape(10, 10)[:, L["d"]]
+    assert np.all((d >= 1000) & (d <= 3000))
+    c = W.make_workload("thick_oxide", n_stacks=10, seed_offset=1)
+    assert not np.array_equal(a.params, c.params)
+    full = W.make_workload("thick_oxide")
+    assert full.evals == 16384 * 400 * 21
+
+
+def test_contrast_workload_structure():
+    wl = W.make_workload("oled_cofit", n_stacks=2)
+    assert wl.n_stacks == 6 and list(wl.dataset) == [0, 1, 2, 0, 1, 2]
+    assert list(np.diff(wl.q_off)) == [150, 220, 300]
+    P = W.n_params(10)
+    p = wl.params.reshape(6, P)
+    L = W.layout(10)
+    # layer parameters shared across the three contrasts of a chain
+    np.testing.assert_array_equal(p[0, L["d"]], p[2, L["d"]])
+    assert p[1, L["rho"]][0] == 6.35e-6 and p[2, L["rho"]][-1] == 4.2e-6
+
+
+def test_uneven_workload_ranges():
+    wl = W.make_workload("uneven", n_stacks=200)
+    assert wl.n_layers.min() >= 1 and wl.n_layers.max() <= 20
+    lens = np.diff(wl.q_off)
+    assert lens.min() >= 50 and lens.max() <= 500
+    rel = wl.dq / wl.q
+    assert rel.min() >= 0.0199 and rel.max() <= 0.0801
+
+
+def test_golden_data_match_grids():
+    for name in ("film_1l", "thick_oxide", "oled_cofit", "vi_step"):
+        wl = W.make_workload(name, n_stacks=1)
+        assert np.all(wl.r_err > 0) and np.all(wl.r_obs > 0)
+
+
+# ----------------------------------------------------------------- bench ----
+def test_flop_table_is_monotone_and_positive():
+    import bench
+    f = [bench.flops_per_eval(n, False, 21) for n in range(0, 21)]
+    assert all(x > 0 for x in f)
+    assert all(b > a for a, b in zip(f, f[1:]))
+    assert bench.flops_per_eval(3, True, 17) > bench.flops_per_eval(3, False, 17)
+    assert abs(bench.peak_fp32_tflops() - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9

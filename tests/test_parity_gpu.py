@@ -1,0 +1,365 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs, element by element.
+
+Tolerances (per stack):
+  smeared model m:   max |log m - log m_ref|              <= 1e-5
+  log-likelihood:    |l - l_ref| / |l_ref|                <= 1e-5
+  gradient:          ||(g - g_ref) * typ||_inf / ||g_ref * typ||_inf <= 1e-4
+with typ = (1 A, 1e-6 A^-2, 1e-8 A^-2, 1 A, 1, 1e-7) per parameter class
+(the pre-scaling advice of Sec. 2.3.1).  The plain FP64 path is held to
+1e-12 (log-likelihood), FP32 rounding of its float output (model) and 1e-5
+(its central-difference gradient).
+"""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2509_06924_gb300 as nr
+from paper_2509_06924_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TOL_M, TOL_LL, TOL_G = 1e-5, 1e-5, 1e-4
+
+
+def run_gpu(wl, precision="mixed", modes=("model", "loglik", "grad"), **kw):
+    ctx = nr.Context(n_quad=wl.n_quad, precision=precision, **kw)
+    b = nr.Batch.from_workload(wl)
+    out = {}
+    if "model" in modes:
+        out["m"] = ctx.reflectivity(b).cpu().numpy().astype(np.float64)
+    if "loglik" in modes:
+        out["ll"] = ctx.loglik(b).cpu().numpy()
+    if "grad" in modes:
+        ll, g = ctx.loglik_grad(b)
+        out["ll_g"], out["g"] = ll.cpu().numpy(), g.cpu().numpy()
+    out["flags"] = ctx.device_status()
+    ctx.close()
+    return out
+
+
+def run_oracle(wl, modes=("model", "grad")):
+    out = {}
+    if "model" in modes:
+        out["m"] = oracle.batch("model", wl.n_layers, wl.params, wl.dataset, wl.q_off, wl.q, wl.dq, None, None,
+                                wl.n_quad)
+    if "grad" in modes:
+        out["ll"], out["g"] = oracle.batch("grad", wl.n_layers, wl.params, wl.dataset, wl.q_off, wl.q, wl.dq,
+                                           wl.r_obs, wl.r_err, wl.n_quad)
+    return out
+
+
+def grad_err(wl, g, g_ref, stacks=None):
+    po = wl.par_off
+    worst = 0.0
+    for s in (range(wl.n_stacks) if stacks is None else stacks):
+        typ = W.typical_scale(int(wl.n_layers[s]))
+        a, b = g[po[s]:po[s + 1]] * typ, g_ref[po[s]:po[s + 1]] * typ
+        den = np.max(np.abs(b))
+        worst = max(worst, float(np.max(np.abs(a - b)) / den) if den > 0 else float(np.max(np.abs(a))))
+    return worst
+
+
+def assert_parity(wl, gpu, ref, tol_m=TOL_M, tol_ll=TOL_LL, tol_g=TOL_G):
+    assert gpu["flags"] == 0
+    if "m" in gpu and "m" in ref:
+        assert np.all(np.isfinite(gpu["m"]))
+        e = np.max(np.abs(np.log(gpu["m"]) - np.log(ref["m"]))) if gpu["m"].size else 0.0
+        assert e <= tol_m, f"model: max |dlog m| {e:.3e}"
+    if "ll" in gpu:
+        e = np.max(np.abs(gpu["ll"] - ref["ll"]) / np.maximum(np.abs(ref["ll"]), 1e-300))
+        assert e <= tol_ll, f"loglik: rel {e:.3e}"
+    if "g" in gpu:
+        e = np.max(np.abs(gpu["ll_g"] - ref["ll"]) / np.maximum(np.abs(ref["ll"]), 1e-300))
+        assert e <= tol_ll, f"loglik (grad call): rel {e:.3e}"
+        e = grad_err(wl, gpu["g"], ref["g"])
+        assert e <= tol_g, f"gradient: scaled {e:.3e}"
+
+
+# ------------------------------------------------------------ workloads ----
+# sizes the oracle finishes in seconds, spanning several CTA tiles and a
+# ragged last tile (400 = 33 x 12 + 4 for K = 21, 200 = 13 x 15 + 5 for K = 17)
+SMALL = [("film_1l", 96), ("thick_oxide", 128), ("oled_cofit", 8), ("uneven", 48), ("vi_step", 4)]
+
+
+@pytest.mark.parametrize("name,S", SMALL)
+def test_mixed_parity_small(name, S):
+    wl = W.make_workload(name, n_stacks=S)
+    assert_parity(wl, run_gpu(wl), run_oracle(wl))
+
+
+@pytest.mark.parametrize("name,S", [("film_1l", 8), ("thick_oxide", 8), ("oled_cofit", 2), ("uneven", 10)])
+def test_fp64_plain_parity(name, S):
+    wl = W.make_workload(name, n_stacks=S)
+    gpu = run_gpu(wl, precision="fp64")
+    ref = run_oracle(wl)
+    assert gpu["flags"] == 0
+    # model output is float32: its rounding only
+    np.testing.assert_allclose(gpu["m"], ref["m"], rtol=1.2e-7, atol=0)
+    np.testing.assert_allclose(gpu["ll"], ref["ll"], rtol=1e-12)
+    np.testing.assert_array_equal(gpu["ll"], gpu["ll_g"])
+    # central differences with h = eps^(1/3) typ: truncation error
+    assert grad_err(wl, gpu["g"], ref["g"]) <= 1e-5
+
+
+# full-size workloads in the launch configuration the benchmark times;
+# sampled stacks are compared with the oracle one by one
+FULL = [("thick_oxide", 64), ("film_1l", 48), ("oled_cofit", 12), ("uneven", 12), ("vi_step", 6)]
+
+
+@pytest.mark.parametrize("name,samples", FULL)
+def test_mixed_parity_full_size_sampled(name, samples):
+    wl = W.make_workload(name)
+    gpu = run_gpu(wl, modes=("grad",))
+    assert gpu["flags"] == 0
+    assert np.all(np.isfinite(gpu["g"])) and np.all(np.isfinite(gpu["ll_g"]))
+    rng = np.random.default_rng(20250906)
+    stacks = np.sort(rng.choice(wl.n_stacks, size=min(samples, wl.n_stacks), replace=False))
+    sub = wl.subset(stacks)
+    ref = run_oracle(sub, modes=("grad",))
+    po = wl.par_off
+    g = np.concatenate([gpu["g"][po[s]:po[s + 1]] for s in stacks])
+    ll = gpu["ll_g"][stacks]
+    assert np.max(np.abs(ll - ref["ll"]) / np.abs(ref["ll"])) <= TOL_LL
+    assert grad_err(sub, g, ref["g"]) <= TOL_G
+    # a property that holds for every stack: only SLD differences matter,
+    # so d/d rho_0 = -sum_j d/d rho_j
+    for s in range(0, wl.n_stacks, max(1, wl.n_stacks // 4096)):
+        n = int(wl.n_layers[s])
+        gr = gpu["g"][po[s]:po[s + 1]][W.layout(n)["rho"]]
+        assert abs(gr[0] + gr[1:].sum()) <= 1e-9 * np.abs(gr).max() + 1e-300
+
+
+def test_full_size_is_deterministic():
+    wl = W.make_workload("thick_oxide")
+    ctx = nr.Context(n_quad=wl.n_quad)
+    b = nr.Batch.from_workload(wl)
+    ll1, g1 = ctx.loglik_grad(b)
+    ll2, g2 = ctx.loglik_grad(b)
+    assert torch.equal(ll1, ll2) and torch.equal(g1, g2)
+    assert ctx.device_status() == 0
+
+
+# ----------------------------------------------------------- edge cases ----
+def custom_workload(stacks, datasets, K=17, data_from_oracle=True):
+    """stacks: list of (n, packed params, dataset index); datasets: list of
+    (Q, dQ) arrays.  Data: oracle model of the first stack on each dataset
+    x 1.03, e = 5 %."""
+    q_off = np.concatenate([[0], np.cumsum([len(q) for q, _ in datasets])]).astype(np.int64)
+    q = np.concatenate([np.asarray(q, np.float32) for q, _ in datasets]) if datasets else np.zeros(0, np.float32)
+    dq = np.concatenate([np.asarray(d, np.float32) for _, d in datasets]) if datasets else np.zeros(0, np.float32)
+    r_obs = np.ones_like(q)
+    r_err = np.full_like(q, 0.05)
+    if data_from_oracle:
+        for di in range(len(datasets)):
+            a, b = int(q_off[di]), int(q_off[di + 1])
+            owner = [s for s in stacks if s[2] == di]
+            if owner and b > a:
+                m = oracle.model(owner[0][0], owner[0][1], q[a:b], dq[a:b], K)
+                r_obs[a:b] = (1.03 * m).astype(np.float32)
+                r_err[a:b] = (0.05 * m).astype(np.float32)
+    return W.Workload("custom", np.array([s[0] for s in stacks], np.int32),
+                      np.concatenate([s[1] for s in stacks]), np.array([s[2] for s in stacks], np.int32),
+                      q_off, q, dq, r_obs, r_err, K)
+
+
+def rand_stack(rng, n, front=0.0, back=2.07e-6, d_range=(20, 400), absorbing=True):
+    d = rng.uniform(*d_range, n)
+    rho = rng.uniform(-0.5e-6, 6.5e-6, n)
+    iota = rng.uniform(0, 1e-8, n) if absorbing else np.zeros(n)
+    sig = rng.uniform(0, 15, n + 1)
+    return W.pack(d, np.concatenate([[front], rho, [back]]), np.concatenate([iota, [0.0]]), sig,
+                  rng.uniform(0.9, 1.1), rng.uniform(1e-8, 1e-6))
+
+
+def test_bare_substrates_mixed_with_films():
+    rng = np.random.default_rng(1)
+    grid = (W.log_grid(123, 0.004, 0.3), 0.04 * W.log_grid(123, 0.004, 0.3))
+    stacks = [(0, W.pack([], [0.0, 2.07e-6], [0.0], [4.0], 1.0, 1e-7), 0),
+              (1, rand_stack(rng, 1), 0),
+              (0, W.pack([], [6.35e-6, 2.07e-6], [1e-9], [0.0], 1.0, 5e-7), 0)]
+    wl = custom_workload(stacks, [grid])
+    assert_parity(wl, run_gpu(wl), run_oracle(wl))
+
+
+def test_deep_stacks_every_bucket():
+    rng = np.random.default_rng(2)
+    grid = (W.log_grid(77, 0.005, 0.25), 0.05 * W.log_grid(77, 0.005, 0.25))
+    ns = [2, 3, 5, 9, 13, 17, 20]           # one stack in every register bucket up to 20 layers
+    stacks = [(n, rand_stack(rng, n), 0) for n in ns]
+    wl = custom_workload(stacks, [grid])
+    assert_parity(wl, run_gpu(wl), run_oracle(wl))
+
+
+def test_stacks_deeper_than_the_workloads():
+    """21..64 layers (beyond every workload): the FP32 recursion error grows
+    with depth, so the model bound scales as 1e-5 * n / 20 there."""
+    rng = np.random.default_rng(4)
+    grid = (W.log_grid(77, 0.005, 0.25), 0.05 * W.log_grid(77, 0.005, 0.25))
+    ns = [21, 33, 64]
+    stacks = [(n, rand_stack(rng, n, d_range=(5, 60)), 0) for n in ns]
+    wl = custom_workload(stacks, [grid])
+    assert_parity(wl, run_gpu(wl), run_oracle(wl), tol_m=TOL_M * 64 / 20)
+
+
+def test_empty_and_ragged_datasets():
+    rng = np.random.default_rng(3)
+    grids = [(np.zeros(0), np.zeros(0)),
+             (W.log_grid(1, 0.05, 0.05), np.array([0.002])),
+             (W.log_grid(253, 0.005, 0.3), 0.03 * W.log_grid(253, 0.005, 0.3)),
+             (W.log_grid(13, 0.01, 0.2), 0.08 * W.log_grid(13, 0.01, 0.2))]
+    stacks = [(1, rand_stack(rng, 1), 0), (2, rand_stack(rng, 2), 1), (3, rand_stack(rng, 3), 2),
+              (1, rand_stack(rng, 1), 3), (4, rand_stack(rng, 4), 0)]
+    wl = custom_workload(stacks, grids)
+    gpu = run_gpu(wl)
+    ref = run_oracle(wl)
+    assert gpu["flags"] == 0
+    # stacks on the empty dataset: loglik 0 and a zero gradient
+    for s in (0, 4):
+        assert gpu["ll_g"][s] == 0.0 and ref["ll"][s] == 0.0
+        po = wl.par_off
+        assert np.all(gpu["g"][po[s]:po[s + 1]] == 0.0)
+    keep = [1, 2, 3]
+    sub = wl.subset(keep)
+    po = wl.par_off
+    g = np.concatenate([gpu["g"][po[s]:po[s + 1]] for s in keep])
+    assert grad_err(sub, g, run_oracle(sub, modes=("grad",))["g"]) <= TOL_G
+    assert gpu["m"].size == int(wl.out_off[-1])
+    e = np.max(np.abs(np.log(gpu["m"]) - np.log(ref["m"])))
+    assert e <= TOL_M
+
+
+@pytest.mark.parametrize("K", [1, 2, 32])
+def test_quadrature_orders(K):
+    wl = W.make_workload("film_1l", n_stacks=40)
+    wl.n_quad = K
+    assert_parity(wl, run_gpu(wl), run_oracle(wl))
+
+
+def test_zero_resolution_is_unsmeared():
+    wl = W.make_workload("thick_oxide", n_stacks=16)
+    wl.dq = np.zeros_like(wl.dq)
+    assert_parity(wl, run_gpu(wl), run_oracle(wl))
+
+
+def test_quartz_posterior_stack_from_table1():
+    vals = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "quartz_table1.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    p = W.pack([vals["thick_quartz"], vals["thick_oxide"]],
+               [vals["sld_air"], vals["sld_quartz"], vals["sld_oxide"], vals["sld_si"]], [0.0, 0.0, 0.0],
+               [vals["rough_air_quartz"], vals["rough_quartz_oxide"], vals["rough_oxide_si"]],
+               vals["scale"], vals["bkg"])
+    q = W.log_grid(300, 0.006, 0.2)
+    wl = custom_workload([(2, p, 0)], [(q, 0.02 * q.astype(np.float64))], K=21)
+    assert_parity(wl, run_gpu(wl), run_oracle(wl))
+
+
+def test_chunked_matches_unchunked():
+    wl = W.make_workload("oled_cofit", n_stacks=4)
+    a = run_gpu(wl)
+    b = run_gpu(wl, chunk_q=24, tile_q=5)
+    np.testing.assert_array_equal(a["m"], b["m"])
+    np.testing.assert_allclose(b["ll_g"], a["ll_g"], rtol=1e-12)
+    assert grad_err(wl, b["g"], a["g"]) <= 1e-6
+    assert_parity(wl, b, run_oracle(wl))
+
+
+def test_host_memory_calls_match_device_calls():
+    wl = W.make_workload("uneven", n_stacks=20)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    bd = nr.Batch.from_workload(wl)
+    bh = nr.Batch.from_workload(wl, device="cpu", pin=True)
+    lld, gd = ctx.loglik_grad(bd)
+    llh, gh = ctx.loglik_grad(bh)
+    assert not llh.is_cuda
+    assert torch.equal(lld.cpu(), llh) and torch.equal(gd.cpu(), gh)
+    assert torch.equal(ctx.reflectivity(bd).cpu(), ctx.reflectivity(bh))
+    assert torch.equal(ctx.loglik(bd).cpu(), ctx.loglik(bh))
+
+
+def test_autograd_function_backward_is_the_exact_gradient():
+    wl = W.make_workload("film_1l", n_stacks=12)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    b = nr.Batch.from_workload(wl)
+    params = b.params.clone().requires_grad_(True)
+    ll = nr.loglik_autograd(params, ctx, b)
+    w = torch.linspace(0.5, 2.0, wl.n_stacks, dtype=torch.float64, device=ll.device)
+    (ll * w).sum().backward()
+    _, g = ctx.loglik_grad(b)
+    per = torch.as_tensor(4 * wl.n_layers.astype(np.int64) + 6, device=g.device)
+    torch.testing.assert_close(params.grad, g * torch.repeat_interleave(w, per), rtol=0, atol=0)
+
+
+def test_device_data_errors_raise_flags_not_faults():
+    wl = W.make_workload("film_1l", n_stacks=3)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    b = nr.Batch.from_workload(wl)
+    bad_err = b.r_err.clone()
+    bad_err[5] = 0.0
+    ll = ctx.loglik(nr.Batch(b.n_layers, b.dataset, b.q_off, b.params, b.q, b.dq, b.r_obs, bad_err))
+    assert ctx.device_status() & nr.NR_FLAG_BAD_ERR
+    assert not torch.isfinite(ll).all()
+    bad_p = b.params.clone()
+    bad_p[3] = float("nan")
+    ctx.loglik_grad(b.with_params(bad_p))
+    assert ctx.device_status() & nr.NR_FLAG_NONFINITE_PARAM
+    bad_q = b.dq.clone()
+    bad_q[0] = 10.0    # nodes at q <= 0
+    m = ctx.reflectivity(nr.Batch(b.n_layers, b.dataset, b.q_off, b.params, b.q, bad_q))
+    assert ctx.device_status() & nr.NR_FLAG_BAD_Q
+    assert not torch.isfinite(m[0])
+    # the context stays usable and clean afterwards
+    ll2, _ = ctx.loglik_grad(b)
+    assert ctx.device_status() == 0 and torch.isfinite(ll2).all()
+
+
+def test_metadata_validation():
+    wl = W.make_workload("film_1l", n_stacks=2)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    b = nr.Batch.from_workload(wl)
+    for bad in (dict(n_layers=np.array([1, 65], np.int32)), dict(dataset=np.array([0, 1], np.int32)),
+                dict(q_off=np.array([0, -1], np.int64))):
+        fields = dict(n_layers=b.n_layers, dataset=b.dataset, q_off=b.q_off)
+        fields.update(bad)
+        bb = nr.Batch(fields["n_layers"], fields["dataset"], fields["q_off"], b.params, b.q, b.dq, b.r_obs, b.r_err)
+        with pytest.raises(nr.NRError) as ei:
+            ctx.loglik(bb)
+        assert ei.value.status == nr.NR_EINVAL
+    with pytest.raises(nr.NRError):
+        ctx.loglik(nr.Batch(b.n_layers, b.dataset, b.q_off, b.params, b.q, b.dq))  # no data
+    # an empty batch is fine
+    e = nr.Batch(np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(1, np.int64), b.params[:0], b.q[:0], b.dq[:0],
+                 b.r_obs[:0], b.r_err[:0])
+    ll, g = ctx.loglik_grad(e)
+    assert ll.numel() == 0 and g.numel() == 0
+
+
+def test_plan_before_capture_and_graph_replay():
+    wl = W.make_workload("thick_oxide", n_stacks=64)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    b = nr.Batch.from_workload(wl)
+    ctx.plan(b)
+    ll = torch.empty(wl.n_stacks, dtype=torch.float64, device="cuda")
+    g = torch.empty(b.params.numel(), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx.loglik_grad(b, ll_out=ll, grad_out=g, stream=s)
+    torch.cuda.synchronize()
+    ref_ll, ref_g = ll.clone(), g.clone()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        ctx.loglik_grad(b, ll_out=ll, grad_out=g, stream=s)
+    ll.zero_()
+    g.zero_()
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(ll, ref_ll) and torch.equal(g, ref_g)
