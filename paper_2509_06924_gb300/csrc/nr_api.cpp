@@ -129,13 +129,16 @@ struct DevBuf {
 
 constexpr int kGradBuckets[] = {1, 2, 4, 8, 12, 16, 20, 32, 64};
 
+// Register buckets: the 1-layer kernels are specialised for exactly one
+// layer (the common thin-film case); bare substrates go to the 2 bucket.
 int grad_bucket(int n)
 {
+    if (n == 1) return 1;
     for (int b : kGradBuckets)
-        if (n <= b) return b;
+        if (b > 1 && n <= b) return b;
     return -1;
 }
-int fwd_bucket(int n) { return n <= 1 ? 1 : 0; }
+int fwd_bucket(int n) { return n == 1 ? 1 : 0; }
 
 struct Group {
     int nmax = 0;

@@ -74,8 +74,8 @@ struct KernelArgs {
 
 // ---- launchers (nr_mixed.cu) ----
 // Mixed-precision kernels.  `nmax` is the register-array capacity bucket of
-// the launch (every stack of the launch has n <= nmax); 0 selects the
-// runtime-n forward kernel (model / loglik modes only).
+// the launch (every stack of the launch has n <= nmax; nmax = 1 means exactly
+// one layer); 0 selects the runtime-n forward kernel (model / loglik modes).
 int mixed_block_threads(int mode, int nmax);
 size_t mixed_dyn_smem(int mode, int nmax);
 cudaError_t mixed_occupancy(int mode, int nmax, int *blocks_per_sm);

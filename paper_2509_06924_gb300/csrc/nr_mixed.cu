@@ -9,15 +9,17 @@
 // float pairs).  Per evaluation (Sec. 2.1 forward model, Sec. 3 smearing):
 //   a1  node   q = Q + dQ x_k / (2 sqrt(ln 2))             double-float
 //   a3  k_j = sqrt(k_0^2 - 4pi(rho_j - rho_0) + 4pi i iota_j)
-//              k_0^2 - c_j in double-float, sqrt + one Newton step
+//              k_0^2 - c_j in double-float, sqrt + one Newton step where a
+//              layer phase needs it
 //   a4  r_j = 4pi(drho_j + i diota_j) / (k_j + k_{j+1})^2 * exp(-2 k_j k_{j+1} s_j^2)
 //              cancellation-free numerator (exactly k_j^2 - k_{j+1}^2)
 //   a5  E_j = exp(2 i k_j d_j): phase 2 Re(k_j) d_j in double-float reduced
 //              mod 2 pi before the FP32 sincos
 //   a6  Parratt recursion from the backing up: X_n = r_n,
 //       X_j = (r_j + X_{j+1} E_{j+1}) / (1 + r_j X_{j+1} E_{j+1}), R = |X_0|^2
-//   a8  smearing: the K node values of a Q point meet in shared memory,
-//   a9  m = scale S + bkg; loglik term accumulated in FP64,
+//   a8  smearing: the K node values of a Q point meet in shared memory (one
+//       barrier per tile, buffers alternate between tiles),
+//   a9  m = scale S + bkg; loglik terms in a float pair, FP64 per item,
 //   a10 dl/dm seeds the adjoint of every node,
 //   a7  adjoint: a top-down sweep over the interfaces using the stored X_j
 //       (and, for 1-2 layers, every stored intermediate; deeper stacks
@@ -38,9 +40,12 @@ namespace {
 constexpr float kInv2Pi = 0.159154943091895335769f;
 constexpr float kTwoPiHi = 6.28318548202514648438f;      // float(2 pi)
 constexpr float kTwoPiLo = -1.74845553146951715e-07f;    // 2 pi - kTwoPiHi
+constexpr float kRoundMagic = 12582912.0f;               // 1.5 * 2^23: x + M - M rounds x to an integer
 constexpr double kFourPiD = 12.566370614359172953850573533118;
 constexpr float kLog2Pi = 1.83787706640934548356f;       // ln(2 pi)
-// |k_j|^2 < kEdgeFrac k_0^2 selects the interior-edge guard of the adjoint
+constexpr unsigned kFull = 0xffffffffu;
+
+// |k_j|^2 < kEdgeFrac k_0^2 selects the interior-edge treatment of the adjoint
 #ifndef NR_EDGE_FRAC
 #define NR_EDGE_FRAC 0.04f
 #endif
@@ -53,6 +58,10 @@ constexpr float kEdgeFrac = NR_EDGE_FRAC;
 #endif
 #ifndef NR_MINB_FWD
 #define NR_MINB_FWD 4
+#endif
+// 1: the 1-layer kernels treat n as the compile-time constant 1
+#ifndef NR_EXACT1
+#define NR_EXACT1 1
 #endif
 
 // ------------------------------------------------------------ primitives --
@@ -100,6 +109,11 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // Re(conj(a) * b)
 __device__ __forceinline__ float redot(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
+__device__ __forceinline__ float2 cdiv(float2 a, float2 b)
+{
+    const float inv = rcp_approx(fmaf(b.x, b.x, b.y * b.y));
+    return cscale(cmulc(b, a), inv);
+}
 
 // z-component of the wavevector in one medium: value (re, im) plus the low
 // word of Re k when the wave propagates (double-float real part).
@@ -108,10 +122,11 @@ struct Kz {
 };
 __device__ __forceinline__ float2 kc(const Kz &k) { return make_float2(k.re, k.im); }
 
-// Principal sqrt of u + i a (u = uh + ul double-float, a >= 0): FP32 root
-// from one rsqrt, then one Newton step on the dominant component, which makes
-// Re k good to double-float accuracy for propagating waves (the phase needs
+// Principal sqrt of u + i a (u = uh + ul double-float, a >= 0) from one
+// rsqrt.  With REFINE, one Newton step on the dominant component makes Re k
+// good to double-float accuracy for propagating waves (a layer phase needs
 // it) and Im k good to FP32 accuracy for evanescent ones.
+template <bool REFINE>
 __device__ __forceinline__ Kz kz_sqrt(float uh, float ul, float a)
 {
     const float au = fabsf(uh);
@@ -122,33 +137,41 @@ __device__ __forceinline__ Kz kz_sqrt(float uh, float ul, float a)
     }
     const float h = fmaxf(0.5f * (au + m), 1e-30f);
     const float rt = rsqrt_approx(h);
-    const float t = h * rt;     // sqrt(h)
+    const float t = h * rt;      // sqrt(h)
     const float i2t = 0.5f * rt; // 1 / (2 sqrt(h))
     const float small = a * i2t;
     const bool prop = uh >= 0.f;
-    const float sgn = prop ? 1.f : -1.f;
-    // residual of big^2 - small^2 = |u| and its Newton correction
-    const float e = fmaf(-t, t, sgn * uh) + fmaf(small, small, sgn * ul);
-    const float corr = e * i2t;
     Kz k;
-    k.re = prop ? t : small;
-    k.im = prop ? small : t + corr;
-    k.lo = prop ? corr : 0.f;
+    if constexpr (REFINE) {
+        const float sgn = prop ? 1.f : -1.f;
+        // residual of big^2 - small^2 = |u| and its Newton correction
+        const float e = fmaf(-t, t, sgn * uh) + fmaf(small, small, sgn * ul);
+        const float corr = e * i2t;
+        k.re = prop ? t : small;
+        k.im = prop ? small : t + corr;
+        k.lo = prop ? corr : 0.f;
+    } else {
+        k.re = prop ? t : small;
+        k.im = prop ? small : t;
+        k.lo = 0.f;
+    }
     return k;
 }
 
 // k of medium j >= 1 from k_0^2 = (p_hi + p_lo) and c_j = 4 pi (rho_j - rho_0).
+template <bool REFINE>
 __device__ __forceinline__ Kz medium_kz(float p_hi, float p_lo, float2 c, float a)
 {
     float uh, ul;
     two_sum(p_hi, -c.x, uh, ul);
     ul = __fadd_rn(ul, __fadd_rn(p_lo, -c.y));
     fast_two_sum(uh, ul, uh, ul);
-    return kz_sqrt(uh, ul, a);
+    return kz_sqrt<REFINE>(uh, ul, a);
 }
 
 // E = exp(2 i k d).  The real phase 2 Re(k) d is formed in double-float and
-// reduced modulo 2 pi (Cody-Waite, two-word 2 pi) before the FP32 sincos.
+// reduced modulo 2 pi (Cody-Waite, two-word 2 pi; the multiple of 2 pi is
+// rounded with the 1.5 * 2^23 addition) before the FP32 sincos.
 __device__ __forceinline__ float2 layer_phase(const Kz &k, float2 d)
 {
     const float t = 2.f * k.re, tl = 2.f * k.lo;
@@ -156,7 +179,7 @@ __device__ __forceinline__ float2 layer_phase(const Kz &k, float2 d)
     float pl = fmaf(t, d.x, -ph);
     pl = fmaf(t, d.y, pl);
     pl = fmaf(tl, d.x, pl);
-    const float nt = rintf(ph * kInv2Pi);
+    const float nt = __fadd_rn(fmaf(ph, kInv2Pi, kRoundMagic), -kRoundMagic);
     float red = fmaf(-nt, kTwoPiHi, ph);
     red = fmaf(-nt, kTwoPiLo, red);
     red += pl;
@@ -198,26 +221,21 @@ __device__ __forceinline__ float2 mobius(float2 r, float2 Y, float2 &D)
     return cmul(cadd(r, Y), D);
 }
 
-
 // ------------------------------------------------- interior critical edges --
-// Near the critical edge of an interior layer (k_j -> 0) the plain adjoint
-// forms d/dk_j as a sum of large terms that cancel and then divides by k_j,
-// which costs FP32 all its digits.  The reflectivity is an even function of
-// every interior k_j (the rough Fresnel coefficients obey r(-k) = 1/r(k)),
-// so it depends on u_j = k_j^2 only.  This guard evaluates dX_{j-1}/du_j
-// through the layer's symmetrised characteristic matrix
+// Near the critical edge of an interior layer (k_j -> 0) the Parratt form is
+// 0/0 (r_{j-1} -> 1, r_j -> -1, E_j -> 1) and the plain adjoint forms d/dk_j
+// as a sum of large terms that cancel before dividing by k_j, which costs
+// FP32 all its digits.  The reflectivity is an even function of every
+// interior k_j (the rough Fresnel coefficients obey r(-k) = 1/r(k)), so it
+// depends on u_j = k_j^2 only.  These evaluations take dX_{j-1}/du_j through
+// the layer's symmetrised characteristic matrix
 //   Lambda = I_{j-1} P_j I_j * (rho+_{j-1} rho+_j) / (2 k_j),
-// whose entries are (ab +- u) sinh(k g)/k + (a +- b) cosh(k g) with
-// g = a s1^2 +- b s2^2 +- i d (a = k_{j-1}, b = k_{j+1}), all even in k_j,
-// and differentiates them in u analytically (no cancellation):
-//   X_{j-1} = (L10 + L11 Z) / (L00 + L01 Z),  Z = X_{j+1} E_{j+1}.
-// Returns ubar = conj(dX_{j-1}/du_j) * Xbar_{j-1}.
-__device__ __forceinline__ float2 cdiv(float2 a, float2 b)
-{
-    const float inv = rcp_approx(fmaf(b.x, b.x, b.y * b.y));
-    return cscale(cmulc(b, a), inv);
-}
-
+// with rho+_{j-1} = (a + k) e^{a k s1^2}, rho+_j = (k + b) e^{k b s2^2}; its
+// entries are (ab +- u) sinh(k g)/k + (a +- b) cosh(k g) with
+// g = a s1^2 +- b s2^2 -+ i d (a = k_{j-1}, b = k_{j+1}), all even in k_j,
+// differentiated in u analytically (no cancellation):
+//   X_{j-1} = (L10 + L11 Z) / (L00 + L01 Z),  Z = X_{j+1} E_{j+1}
+// (Z = 0 for the bottom layer, where only L00 and L10 are needed).
 struct Hyp {
     float2 ch, shc, g; // cosh(x), sinh(x)/x, (x cosh x - sinh x)/x^3, all times e^-m
 };
@@ -254,38 +272,37 @@ __device__ __forceinline__ Hyp hyp_scaled(float2 x, float m)
     return h;
 }
 
-template <bool INL>
-__device__ float2 edge_ubar_impl(float2 a, float2 k, float2 b, float s1, float s2, float d, float2 Z,
-                                         float2 Xbar_up)
+// Returns ubar = conj(dX_{j-1}/du_j) * Xbar_{j-1}.
+__device__ __forceinline__ float2 edge_ubar(float2 a, float2 k, float2 b, float s1, float s2, float d, float2 Z,
+                                            bool zzero, float2 Xbar_up)
 {
     const float2 u = csqr(k);
     const float2 ab = cmul(a, b);
     const float2 sp = cadd(cscale(a, s1 * s1), cscale(b, s2 * s2));
     const float2 sq = csub(cscale(a, s1 * s1), cscale(b, s2 * s2));
-    // common scale e^-m, m = max |Re(k g)| over the four exponents
+    // common scale e^-m, m >= max |Re(k g)| over the exponents
     float m = fmaxf(fabsf(fmaf(k.x, sp.x, -k.y * sp.y)), fabsf(fmaf(k.x, sq.x, -k.y * sq.y)));
     m += fabsf(k.y * d);
-    // entry i: 0 chi (L00), 1 nu (L01), 2 phi (L10), 3 psi (L11); streamed into
-    // den = L00 + L01 Z, dden = L00' + L01' Z, xn = L10 + L11 Z, dxn = L10' + L11' Z
+    // entry i: 0 chi (L00), 1 phi (L10), 2 nu (L01), 3 psi (L11); streamed
+    // into den = L00 + L01 Z, dden, xn = L10 + L11 Z, dxn
     float2 den = make_float2(0.f, 0.f), dden = den, xn = den, dxn = den;
+    const int ne = zzero ? 2 : 4;
 #pragma unroll 1
-    for (int i = 0; i < 4; ++i) {
-        const bool plus = (i == 0 || i == 3);
+    for (int i = 0; i < ne; ++i) {
+        const bool plus = (i == 0 || i == 3);                   // (ab+u) S + (a+b) C
         const float2 base = plus ? sp : sq;
-        const float2 g = make_float2(base.x, (i == 0 || i == 1) ? base.y - d : base.y + d);
+        const float2 g = make_float2(base.x, (i == 0 || i == 2) ? base.y - d : base.y + d);
         const Hyp h = hyp_scaled(cmul(k, g), m);
         const float2 g2 = csqr(g);
         const float2 S = cmul(g, h.shc);                        // sinh(kg)/k
         const float2 dC = cscale(cmul(g2, h.shc), 0.5f);        // d cosh(kg)/du
         const float2 dS = cscale(cmul(cmul(g2, g), h.g), 0.5f); // d (sinh(kg)/k)/du
-        const float sgn = plus ? 1.f : -1.f;                    // (ab+u) or -(ab-u)
-        const float2 f = plus ? cadd(ab, u) : csub(u, ab);
+        const float2 f = plus ? cadd(ab, u) : csub(u, ab);      // (ab+u) or -(ab-u)
         const float2 cfac = plus ? cadd(a, b) : csub(a, b);     // (a+b) or (a-b)
         const float2 L = cadd(cmul(f, S), cmul(cfac, h.ch));
-        const float2 dL = cadd(cscale(S, 1.f), cadd(cmul(f, dS), cmul(cfac, dC)));
-        (void)sgn;
-        const float2 w = (i == 1 || i == 3) ? Z : make_float2(1.f, 0.f);
-        if (i < 2) {
+        const float2 dL = cadd(S, cadd(cmul(f, dS), cmul(cfac, dC)));
+        const float2 w = (i >= 2) ? Z : make_float2(1.f, 0.f);
+        if (i == 0 || i == 2) {
             den = cadd(den, cmul(w, L));
             dden = cadd(dden, cmul(w, dL));
         } else {
@@ -297,15 +314,24 @@ __device__ float2 edge_ubar_impl(float2 a, float2 k, float2 b, float s1, float s
     const float2 dXdu = cdiv(csub(dxn, cmul(X, dden)), den);
     return cmulc(dXdu, Xbar_up);
 }
-__device__ __noinline__ float2 edge_ubar_call(float2 a, float2 k, float2 b, float s1, float s2, float d, float2 Z,
-                                              float2 Xbar_up)
+
+// Drains `cnt` queued interior-edge entries of one warp (one per lane) into
+// per-thread partials kept in shared memory (acc points at this thread's
+// slot of medium 1's Re-accumulator; stride between accumulators `stride`,
+// Re -> Im distance `im_off`).  Kept out of line so that the rolled sweep
+// it is called from keeps its register budget.
+template <int EQ>
+__device__ __noinline__ void eq_drain_smem(float2 (*q)[EQ], const int *qj, const float *sg, const float2 *dd, int n,
+                                           int lane, int cnt, float *acc, int stride, int im_off)
 {
-    return edge_ubar_impl<false>(a, k, b, s1, s2, d, Z, Xbar_up);
-}
-__device__ __forceinline__ float2 edge_ubar_inline(float2 a, float2 k, float2 b, float s1, float s2, float d,
-                                                   float2 Z, float2 Xbar_up)
-{
-    return edge_ubar_impl<true>(a, k, b, s1, s2, d, Z, Xbar_up);
+    if (lane < cnt) {
+        const int j = qj[lane];
+        const float2 ub = edge_ubar(q[0][lane], q[1][lane], q[2][lane], sg[j - 1], sg[j], dd[j].x, q[3][lane],
+                                    j == n, q[4][lane]);
+        // conj(kbar)/k_j = 2 conj(ubar)
+        acc[(j - 1) * stride] += 2.f * ub.x;
+        acc[(j - 1) * stride + im_off] += -2.f * ub.y;
+    }
 }
 
 // --------------------------------------------------------------- traits ---
@@ -313,20 +339,27 @@ template <int MODE, int NMAX>
 struct Traits {
     static constexpr bool kGradMode = MODE == kGrad;
     static constexpr int NM = NMAX > 0 ? NMAX : NR_MAX_LAYERS; // smem capacity
-    // per-thread partials live in shared memory for NMAX >= 8; the block
-    // shrinks for deep buckets so that they still fit
-    static constexpr int BLOCK = !kGradMode ? 256 : NMAX >= 32 ? 128 : 256;
+    // deep gradient buckets run 128-thread CTAs so that their per-thread
+    // state in shared memory still leaves room for several CTAs per SM
+    static constexpr int BLOCK = !kGradMode ? 256 : NMAX >= 16 ? 128 : 256;
     static constexpr bool STORE = kGradMode && NMAX <= 2;     // keep all intermediates
-    static constexpr bool SMEM_ACC = kGradMode && NMAX >= 8;  // per-thread partials in smem
-    static constexpr bool UNROLL = NMAX >= 1 && NMAX <= 20;   // register arrays
+    static constexpr bool UNROLL = NMAX >= 1 && NMAX <= 4;    // register arrays, unrolled sweeps
+    static constexpr bool SMEM_ACC = kGradMode && !UNROLL;    // partials in shared memory
+    static constexpr bool X_SMEM = kGradMode && !UNROLL;      // X_j in shared memory
     static constexpr int NACC = kGradMode ? 4 * NM + 3 : 0;   // partial gradients per thread
     static constexpr int NRAW = 4 * NM + 6;
     static constexpr int WARPS = BLOCK / 32;
-    // the 1-layer bucket runs the interior-edge guard after the adjoint sweep
-    // (inlined, little else live); deeper buckets call it in the sweep
-    static constexpr bool EDGE_DEFER = kGradMode && NMAX == 1;
-    // shallow gradient buckets: cap registers so that 4 CTAs fit on an SM
-    static constexpr int MINB = !kGradMode ? NR_MINB_FWD : NMAX == 1 ? NR_MINB_GRAD1 : NMAX <= 20 ? 2 : 4;
+    // interior-edge work queue per warp: unrolled kernels drain it after each
+    // tile's sweep, rolled ones inside the sweep
+    static constexpr int EQ_CAP = !kGradMode ? 1 : UNROLL ? 32 * NM + 32 : 64;
+#ifndef NR_DEEP_REGS
+#define NR_DEEP_REGS 96
+#endif
+    // register caps: rolled deep kernels are held to NR_DEEP_REGS per thread
+    static constexpr int MINB = !kGradMode ? NR_MINB_FWD : NMAX == 1 ? NR_MINB_GRAD1 : NMAX <= 4 ? 3
+                                : 65536 / (BLOCK * NR_DEEP_REGS);
+    static constexpr size_t DYN = (SMEM_ACC ? (size_t)NACC * BLOCK * 4 : 0) +
+                                  (X_SMEM ? (size_t)(NM + 1) * BLOCK * 8 : 0);
 };
 
 // Per-stack parameters staged in shared memory.
@@ -430,20 +463,26 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     constexpr int BLOCK = T::BLOCK;
     constexpr bool GRAD = T::kGradMode;
     constexpr bool LIK = MODE != kModel;
+    constexpr int EQ = T::EQ_CAP;
 
     __shared__ StackSmem<NM> sm;
-    __shared__ float sh_wR[2][BLOCK];   // w_k R per evaluation, double-buffered by tile
-    __shared__ float sh_seed[2][BLOCK]; // scale * dl/dm per Q slot
+    __shared__ float sh_wR[2][2 * BLOCK]; // w_k R per (Q slot, node), double-buffered
     __shared__ double sh_red[T::WARPS][32];
     __shared__ double sh_redd[T::WARPS][4];
     __shared__ double sh_raw[T::NRAW];
     __shared__ int sh_item;
     __shared__ int sh_last;
-    extern __shared__ float sh_acc[]; // [NACC][BLOCK] per-thread partials when SMEM_ACC
+    // interior-edge queue per warp: a, k, b, Z, Xbar (complex) and the medium
+    __shared__ float2 sh_eq[GRAD ? T::WARPS : 1][5][EQ];
+    __shared__ int sh_eqj[GRAD ? T::WARPS : 1][EQ];
+    extern __shared__ __align__(16) float sh_dyn[]; // [NACC][BLOCK] partials, then [NM+1][BLOCK] X_j
+    float *sh_acc = sh_dyn;
+    float2 *sh_X = reinterpret_cast<float2 *>(sh_dyn + (T::SMEM_ACC ? T::NACC * BLOCK : 0));
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int K = qc.K;
+    const int KP = K;            // node stride of a Q slot in sh_wR
     const int TQ = ka.tile_q;
     const int qslot = tid / K;
     const int kn = tid - qslot * K;
@@ -451,10 +490,14 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     const float g_hi = lane_on ? qc.g_hi[kn] : 0.f;
     const float g_lo = lane_on ? qc.g_lo[kn] : 0.f;
     const float wk = lane_on ? qc.w[kn] : 0.f;
-    // per-Q lanes: kSubLanes threads per Q slot of the tile
-    const int qgrp = tid / kSubLanes, qpart = tid - qgrp * kSubLanes;
-    const bool qlane = qgrp < TQ;
-    const int qwarps = (TQ * kSubLanes + 31) / 32;
+    // the warp's Q slots for the smearing sums and the lanes per slot
+    // (sgl depends on K only, so a Q point's sum has the same order in every
+    // warp and tile shape)
+    const int qs0 = (warp * 32) / K;
+    const int nslots = (31 + K - 1) / K + 1; // most slots any warp touches
+    const int sgl = nslots <= 1 ? 32 : nslots <= 2 ? 16 : nslots <= 4 ? 8 : nslots <= 8 ? 4 : nslots <= 16 ? 2 : 1;
+
+    for (int i = tid; i < 4 * BLOCK; i += BLOCK) (&sh_wR[0][0])[i] = 0.f; // padding stays 0
 
     for (;;) {
         if (tid == 0) sh_item = atomicAdd(&ka.ticket[0], 1);
@@ -463,7 +506,8 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
         if (item >= ka.n_items) break;
         const WorkItem wi = ka.items[item];
         const StackInfo si = ka.stacks[wi.stack];
-        const int n = si.n;
+        // the 1-layer bucket holds exactly-1-layer stacks: n is a constant there
+        const int n = (NMAX == 1 && NR_EXACT1) ? 1 : si.n;
         const double *p = ka.params + si.par_off;
         stage_stack<NM>(sm, p, n, tid, ka.status);
 
@@ -471,26 +515,62 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
         float accr[GRAD && !T::SMEM_ACC ? T::NACC : 1];
         if constexpr (GRAD) {
             if constexpr (T::SMEM_ACC) {
-                for (int i = 0; i < 4 * n + 3; ++i) {
-                    const int idx = i < n ? i
-                                    : i < 2 * n + 1 ? NM + (i - n)
-                                    : i < 3 * n + 2 ? 2 * NM + 1 + (i - 2 * n - 1)
-                                                    : 3 * NM + 2 + (i - 3 * n - 2);
-                    sh_acc[idx * BLOCK + tid] = 0.f;
-                }
+                for (int i = 0; i < T::NACC; ++i) sh_acc[i * BLOCK + tid] = 0.f;
             } else {
 #pragma unroll
                 for (int i = 0; i < T::NACC; ++i) accr[i] = 0.f;
             }
         }
+        constexpr int oD = 0, oUr = NM, oUi = 2 * NM + 1, oS = 3 * NM + 2;
         auto acc_add = [&](int idx, float v) __attribute__((always_inline)) {
             if constexpr (GRAD) {
                 if constexpr (T::SMEM_ACC) sh_acc[idx * BLOCK + tid] += v;
                 else accr[idx] += v;
             }
         };
-        constexpr int oD = 0, oUr = NM, oUi = 2 * NM + 1, oS = 3 * NM + 2;
-        // per-Q-lane sums: loglik terms as a float pair, d/dscale, d/dbkg
+        // medium j (runtime) -> its u accumulators
+        auto acc_u = [&](int j, float2 v) __attribute__((always_inline)) {
+            if constexpr (GRAD) {
+                if constexpr (T::SMEM_ACC) {
+                    acc_add(oUr + j - 1, v.x);
+                    acc_add(oUi + j - 1, v.y);
+                } else {
+#pragma unroll
+                    for (int t = 1; t <= NM; ++t)
+                        if (t == j) {
+                            accr[oUr + t - 1] += v.x;
+                            accr[oUi + t - 1] += v.y;
+                        }
+                }
+            }
+        };
+        int eq_cnt = 0; // entries in this warp's interior-edge queue (warp-uniform)
+        // drain `cnt` <= 32 queued entries, one per lane, then shift the rest down
+        auto eq_drain = [&](int cnt) {
+            if constexpr (T::SMEM_ACC) {
+                eq_drain_smem<EQ>(sh_eq[warp], sh_eqj[warp], sm.sg, sm.d, n, lane, cnt, sh_acc + oUr * BLOCK + tid,
+                                  BLOCK, (oUi - oUr) * BLOCK);
+            } else if (lane < cnt) {
+                const int j = sh_eqj[warp][lane];
+                const float2 ub = edge_ubar(sh_eq[warp][0][lane], sh_eq[warp][1][lane], sh_eq[warp][2][lane],
+                                            sm.sg[j - 1], sm.sg[j], sm.d[j].x, sh_eq[warp][3][lane], j == n,
+                                            sh_eq[warp][4][lane]);
+                // conj(kbar)/k_j = 2 conj(ubar)
+                acc_u(j, make_float2(2.f * ub.x, -2.f * ub.y));
+            }
+            __syncwarp();
+            const int rest = eq_cnt - cnt;
+            for (int e = lane; e < rest; e += 32) {
+                const int src = cnt + e;
+#pragma unroll
+                for (int f = 0; f < 5; ++f) sh_eq[warp][f][e] = sh_eq[warp][f][src];
+                sh_eqj[warp][e] = sh_eqj[warp][src];
+            }
+            __syncwarp();
+            eq_cnt = rest;
+        };
+
+        // per-lane sums of the loglik terms (lanes kn == 0), d/dscale, d/dbkg
         float ll_hi = 0.f, ll_lo = 0.f, gsc_acc = 0.f, gbk_acc = 0.f;
 
         // software pipeline: inputs of the next tile are loaded while the
@@ -500,9 +580,11 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
         float Qn = 0.1f, dQn = 0.f, Ron = 0.f, Ren = 1.f;
         {
             const int qi = wi.q_lo + qslot;
-            if (lane_on && qi < wi.q_hi) { Qn = __ldg(qp + qi); dQn = __ldg(dqp + qi); }
-            const int qj = wi.q_lo + qgrp;
-            if (LIK && qlane && qpart == 0 && qj < wi.q_hi) { Ron = __ldg(rop + qj); Ren = __ldg(rep + qj); }
+            if (lane_on && qi < wi.q_hi) {
+                Qn = __ldg(qp + qi);
+                dQn = __ldg(dqp + qi);
+                if (LIK) { Ron = __ldg(rop + qi); Ren = __ldg(rep + qi); }
+            }
         }
         __syncthreads();
 
@@ -511,20 +593,14 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
         for (int q0 = wi.q_lo; q0 < wi.q_hi; q0 += TQ, buf ^= 1) {
             const int qi = q0 + qslot;
             const bool act = lane_on && qi < wi.q_hi;
-            const float Qv = Qn, dQv = dQn;
-            float Ro = Ron, ie = 0.f, lterm = 0.f;
-            if (LIK && qlane && qpart == 0) {
-                if (!(Ren > 0.f) && q0 + qgrp < wi.q_hi) atomicOr(ka.status, NR_FLAG_BAD_ERR);
-                ie = 1.0f / Ren;
-                lterm = kLog2Pi + 2.f * logf(Ren);
-            }
+            const float Qv = Qn, dQv = dQn, Ro = Ron, Re = Ren;
             {   // prefetch the next tile
-                const int q1 = q0 + TQ;
-                Qn = 0.1f; dQn = 0.f;
-                if (lane_on && q1 + qslot < wi.q_hi) { Qn = __ldg(qp + q1 + qslot); dQn = __ldg(dqp + q1 + qslot); }
-                if (LIK && qlane && qpart == 0 && q1 + qgrp < wi.q_hi) {
-                    Ron = __ldg(rop + q1 + qgrp);
-                    Ren = __ldg(rep + q1 + qgrp);
+                const int q1 = q0 + TQ + qslot;
+                Qn = 0.1f; dQn = 0.f; Ron = 0.f; Ren = 1.f;
+                if (lane_on && q1 < wi.q_hi) {
+                    Qn = __ldg(qp + q1);
+                    dQn = __ldg(dqp + q1);
+                    if (LIK) { Ron = __ldg(rop + q1); Ren = __ldg(rep + q1); }
                 }
             }
             // a1: node position in double-float, k_0 = q/2, k_0^2
@@ -549,15 +625,26 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             Kz kst[T::STORE ? NM + 2 : 1];
             float2 rst[T::STORE ? NM + 1 : 1], Gst[T::STORE ? NM + 1 : 1];
             float2 Est[T::STORE ? NM + 2 : 1], Dst[T::STORE ? NM + 1 : 1];
-            float2 X[GRAD ? NM + 1 : 1];
-            Kz kbelow = medium_kz(p_hi, p_lo, sm.c[n + 1], sm.a[n + 1]);
+            float2 Xr[GRAD && T::UNROLL ? NM + 1 : 1];
+            auto Xput = [&](int j, float2 v) __attribute__((always_inline)) {
+                if constexpr (GRAD) {
+                    if constexpr (T::X_SMEM) sh_X[j * BLOCK + tid] = v;
+                    else Xr[j] = v;
+                }
+            };
+            auto Xget = [&](int j) __attribute__((always_inline)) -> float2 {
+                if constexpr (T::X_SMEM) return sh_X[j * BLOCK + tid];
+                else if constexpr (GRAD) return Xr[j];
+                else return make_float2(0.f, 0.f);
+            };
+            Kz kbelow = medium_kz<false>(p_hi, p_lo, sm.c[n + 1], sm.a[n + 1]);
             float2 Xbelow = make_float2(0.f, 0.f);
             auto fwd_step = [&](int j) __attribute__((always_inline)) {
                 Kz kj;
                 if (j == 0) {
                     kj.re = k0h; kj.im = 0.f; kj.lo = k0l;
                 } else {
-                    kj = medium_kz(p_hi, p_lo, sm.c[j], sm.a[j]);
+                    kj = medium_kz<true>(p_hi, p_lo, sm.c[j], sm.a[j]);
                 }
                 float2 Gj;
                 const float2 rj = fresnel_nc(kc(kj), kc(kbelow), sm.N[j], sm.s[j], Gj);
@@ -572,7 +659,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     if constexpr (T::STORE) { Est[j + 1] = Ej; Dst[j] = Dj; }
                 }
                 if constexpr (T::STORE) { kst[j] = kj; rst[j] = rj; Gst[j] = Gj; }
-                if constexpr (GRAD) X[j] = Xj;
+                Xput(j, Xj);
                 Xbelow = Xj;
                 kbelow = kj;
             };
@@ -587,55 +674,58 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             float R = Xbelow.x * Xbelow.x + Xbelow.y * Xbelow.y;
             if (!qok) R = __int_as_float(0x7fffffff);
 
-            // a8-a10: smearing sum per Q point (kSubLanes lanes each), model,
-            // likelihood, adjoint seed
-            sh_wR[buf][tid] = act ? wk * R : 0.f;
+            // a8-a10: smearing sum, model, likelihood, adjoint seed.  Every
+            // lane of a Q point forms the same sum from shared memory, so the
+            // seed needs no second barrier.
+            if (lane_on) sh_wR[buf][qslot * KP + kn] = act ? wk * R : 0.f;
             __syncthreads();
-            if (warp < qwarps) {
-                float S = 0.f;
-                if (qlane)
-                    for (int k = qpart; k < K; k += kSubLanes) S += sh_wR[buf][qgrp * K + k];
-                S += __shfl_xor_sync(0xffffffffu, S, 1);
-                S += __shfl_xor_sync(0xffffffffu, S, 2);
-                const int qj = q0 + qgrp;
-                if (qlane && qpart == 0) {
-                    float seed = 0.f;
-                    if (qj < wi.q_hi) {
-                        const float m = fmaf(scale, S, bkg);
-                        if constexpr (MODE == kModel) {
-                            ka.r_out[si.out_off + qj] = m;
-                        } else {
-                            const float res = (m - Ro) * ie;
-                            float t1, t2;
-                            two_sum(ll_hi, fmaf(res, res, lterm), t1, t2);
-                            ll_hi = t1;
-                            ll_lo += t2;
-                            if constexpr (GRAD) {
-                                const float dldm = -res * ie;
-                                gsc_acc = fmaf(dldm, S, gsc_acc);
-                                gbk_acc += dldm;
-                                seed = scale * dldm;
-                            }
-                        }
+            float Rb = 0.f;
+            // smearing sums of the Q slots this warp touches: sgl lanes per
+            // slot add strided nodes, a shuffle tree finishes, and every lane
+            // picks its own slot's sum (same order in every warp)
+            float S;
+            {
+                const int g = lane / sgl, part = lane - g * sgl;
+                const int slot = qs0 + g;
+                float ps = 0.f;
+                if (slot < TQ)
+                    for (int k = part; k < K; k += sgl) ps += sh_wR[buf][slot * KP + k];
+                for (int o = 1; o < sgl; o <<= 1) ps += __shfl_xor_sync(kFull, ps, o);
+                S = __shfl_sync(kFull, ps, ((qslot - qs0) * sgl) & 31);
+            }
+            if (act && (GRAD || kn == 0)) {
+                const float m = fmaf(scale, S, bkg);
+                if constexpr (MODE == kModel) {
+                    ka.r_out[si.out_off + qi] = m;
+                } else {
+                    const float ie = rcp_approx(Re);
+                    const float res = (m - Ro) * ie;
+                    if (kn == 0) {
+                        if (!(Re > 0.f)) atomicOr(ka.status, NR_FLAG_BAD_ERR);
+                        float t1, t2;
+                        two_sum(ll_hi, fmaf(res, res, kLog2Pi + 2.f * logf(Re)), t1, t2);
+                        ll_hi = t1;
+                        ll_lo += t2;
                     }
-                    if constexpr (GRAD) sh_seed[buf][qgrp] = seed;
+                    if constexpr (GRAD) {
+                        const float dldm = -res * ie;
+                        if (kn == 0) {
+                            gsc_acc = fmaf(dldm, S, gsc_acc);
+                            gbk_acc += dldm;
+                        }
+                        Rb = wk * scale * dldm;
+                    }
                 }
             }
             if constexpr (GRAD) {
-                __syncthreads();
-                const float Rb = act ? wk * sh_seed[buf][qslot] : 0.f;
-
                 // a7: adjoint sweep from the fronting down to the backing
-                float2 Xb = cscale(X[0], 2.f * Rb);
+                float2 Xb = cscale(Xget(0), 2.f * Rb);
                 float2 kbar = make_float2(0.f, 0.f); // adjoint of k_j (j >= 1)
                 Kz kj;
                 kj.re = k0h; kj.im = 0.f; kj.lo = k0l;
                 Kz kjm1 = kj;                          // k_{j-1}
                 float2 Xb_up = make_float2(0.f, 0.f);  // adjoint of X_{j-1}
                 const float edge_u = kEdgeFrac * k0h * k0h;
-                // deferred guard inputs (1-layer bucket: only medium 1 can be interior)
-                bool edge_pending = false;
-                float2 e_a, e_k, e_b, e_Z, e_Xb;
                 auto adj_step = [&](int j) __attribute__((always_inline)) {
                     const float2 Xb_in = Xb;
                     float2 Zj = make_float2(0.f, 0.f);
@@ -646,20 +736,22 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         rj = rst[j];
                         Gj = Gst[j];
                     } else {
-                        kj1 = medium_kz(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1]);
+                        kj1 = (j == n) ? medium_kz<false>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1])
+                                       : medium_kz<true>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1]);
                         rj = fresnel_nc(kc(kj), kc(kj1), sm.N[j], sm.s[j], Gj);
                     }
                     float2 kbar1 = make_float2(0.f, 0.f);
                     float2 rb;
                     if (j < n) {
+                        const float2 X1 = Xget(j + 1);
                         float2 Ej1, Dj, Y;
                         if constexpr (T::STORE) {
                             Ej1 = Est[j + 1];
                             Dj = Dst[j];
-                            Y = cmul(X[j + 1], Ej1);
+                            Y = cmul(X1, Ej1);
                         } else {
                             Ej1 = layer_phase(kj1, sm.d[j + 1]);
-                            Y = cmul(X[j + 1], Ej1);
+                            Y = cmul(X1, Ej1);
                             const float2 rY = cmul(rj, Y);
                             const float dx = 1.f + rY.x, dy = rY.y;
                             const float inv = rcp_approx(fmaf(dx, dx, dy * dy));
@@ -672,7 +764,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         const float2 dXdY = cmul(csub(one, csqr(rj)), D2);
                         rb = cmulc(dXdr, Xb);
                         const float2 Yb = cmulc(dXdY, Xb);
-                        const float2 Eb = cmulc(X[j + 1], Yb);
+                        const float2 Eb = cmulc(X1, Yb);
                         const float2 Xb1 = cmulc(Ej1, Yb);
                         const float2 iE = make_float2(-Ej1.y, Ej1.x);
                         acc_add(oD + j, redot(Eb, cmul(kc(kj1), iE)));           // d_{j+1}
@@ -689,20 +781,30 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     acc_add(oS + j, redot(rb, cmul(rj, cmul(kc(kj), kc(kj1)))));
                     if (j >= 1) {
                         kbar = cadd(kbar, cmulc(dr_dkj, rb));
-                        // k_j complete: accumulate conj(kbar) / k_j
+                        // k_j complete: accumulate conj(kbar) / k_j, or queue
+                        // the interior-edge evaluation for this lane
                         const float m2 = fmaf(kj.re, kj.re, kj.im * kj.im);
-                        if (m2 < edge_u) {
-                            // interior critical edge: conj(kbar)/k_j = 2 conj(ubar)
-                            if constexpr (T::EDGE_DEFER) {
-                                edge_pending = true;
-                                e_a = kc(kjm1); e_k = kc(kj); e_b = kc(kj1); e_Z = Zj; e_Xb = Xb_up;
-                            } else {
-                                const float2 ub = edge_ubar_call(kc(kjm1), kc(kj), kc(kj1), sm.sg[j - 1],
-                                                                 sm.sg[j], sm.d[j].x, Zj, Xb_up);
-                                acc_add(oUr + j - 1, 2.f * ub.x);
-                                acc_add(oUi + j - 1, -2.f * ub.y);
+                        const bool edge = act && m2 < edge_u;
+                        const unsigned em = __ballot_sync(kFull, edge);
+                        if (em) {
+                            if (edge) {
+                                const int slot = eq_cnt + __popc(em & ((1u << lane) - 1u));
+                                sh_eq[warp][0][slot] = kc(kjm1);
+                                sh_eq[warp][1][slot] = kc(kj);
+                                sh_eq[warp][2][slot] = kc(kj1);
+                                sh_eq[warp][3][slot] = Zj;
+                                sh_eq[warp][4][slot] = Xb_up;
+                                sh_eqj[warp][slot] = j;
                             }
-                        } else {
+                            eq_cnt += __popc(em);
+                            if constexpr (!T::UNROLL) {
+                                if (eq_cnt >= 32) {
+                                    __syncwarp();
+                                    eq_drain(32);
+                                }
+                            }
+                        }
+                        if (!edge) {
                             const float2 kk = cmul(kbar, kc(kj));
                             const float inv = m2 > 0.f ? rcp_approx(m2) : 0.f;
                             acc_add(oUr + j - 1, kk.x * inv);
@@ -725,22 +827,25 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
 #pragma unroll
                     for (int j = 0; j <= NM; ++j)
                         if (j <= n) adj_step(j);
+                    // drain full batches of the interior-edge queue
+                    while (eq_cnt >= 32) {
+                        __syncwarp();
+                        eq_drain(32);
+                    }
                 } else {
 #pragma unroll 1
                     for (int j = 0; j <= n; ++j) adj_step(j);
                 }
-                if constexpr (T::EDGE_DEFER) {
-                    if (edge_pending) {
-                        const float2 ub = edge_ubar_inline(e_a, e_k, e_b, sm.sg[0], sm.sg[1], sm.d[1].x, e_Z, e_Xb);
-                        acc_add(oUr + 0, 2.f * ub.x);
-                        acc_add(oUi + 0, -2.f * ub.y);
-                    }
-                }
             }
-            // no end-of-tile barrier: the next tile uses the other buffers
         }
 
         if constexpr (LIK) {
+            if constexpr (GRAD) {
+                if (eq_cnt > 0) {
+                    __syncwarp();
+                    eq_drain(eq_cnt);
+                }
+            }
             // ---- CTA reduction of the item's partial sums into sh_raw ----
             __syncthreads();
             if constexpr (GRAD && !T::SMEM_ACC) {
@@ -749,7 +854,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 for (int t = 0; t < T::NACC; ++t) {
                     float v = accr[t];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
                     if (lane == 0) sh_red[warp][t] = (double)v;
                 }
                 __syncthreads();
@@ -780,7 +885,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     float v = 0.f;
                     if constexpr (GRAD && T::SMEM_ACC) v = sh_acc[idx * BLOCK + tid];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
                     if (lane == 0) sh_red[warp][c] = (double)v;
                 }
                 __syncthreads();
@@ -791,13 +896,13 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 }
                 __syncthreads();
             }
-            if (warp < qwarps) {   // loglik, d/dscale, d/dbkg live in the per-Q lanes
+            {   // loglik, d/dscale, d/dbkg live in the kn == 0 lanes
                 double a0 = (double)ll_hi + (double)ll_lo, a1 = gsc_acc, a2 = gbk_acc;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-                    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-                    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+                    a0 += __shfl_xor_sync(kFull, a0, o);
+                    a1 += __shfl_xor_sync(kFull, a1, o);
+                    a2 += __shfl_xor_sync(kFull, a2, o);
                 }
                 if (lane == 0) {
                     sh_redd[warp][0] = a0;
@@ -808,7 +913,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             __syncthreads();
             if (tid < 3) {
                 double s = 0.0;
-                for (int w = 0; w < qwarps; ++w) s += sh_redd[w][tid];
+                for (int w = 0; w < T::WARPS; ++w) s += sh_redd[w][tid];
                 sh_raw[4 * n + 3 + tid] = s;
             }
             __syncthreads();
@@ -842,7 +947,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 }
             }
         }
-        __syncthreads(); // sm / sh_raw / sh_item reused by the next item
+        __syncthreads(); // sm / sh_raw / sh_item / sh_wR reused by the next item
     }
     // last CTA out resets the queue for the next launch
     if (tid == 0) {
@@ -857,18 +962,26 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
 }
 
 template <int MODE, int NMAX>
+cudaError_t set_smem_attr()
+{
+    using T = Traits<MODE, NMAX>;
+    if (T::DYN > 48 * 1024)
+        return cudaFuncSetAttribute(nr_mixed_kernel<MODE, NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)T::DYN);
+    return cudaSuccess;
+}
+
+template <int MODE, int NMAX>
 cudaError_t launch_one(int grid, const KernelArgs &a, const QuadConst &qc, cudaStream_t st)
 {
     using T = Traits<MODE, NMAX>;
-    const size_t dyn = T::SMEM_ACC ? (size_t)T::NACC * T::BLOCK * sizeof(float) : 0;
-    static bool attr_done = false; // per-process; the attribute is per function
-    if (!attr_done && dyn > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(nr_mixed_kernel<MODE, NMAX>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    static bool attr_done = false; // per process: the attribute belongs to the function
+    if (!attr_done) {
+        cudaError_t e = set_smem_attr<MODE, NMAX>();
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    nr_mixed_kernel<MODE, NMAX><<<grid, T::BLOCK, dyn, st>>>(a, qc);
+    nr_mixed_kernel<MODE, NMAX><<<grid, T::BLOCK, T::DYN, st>>>(a, qc);
     return cudaGetLastError();
 }
 
@@ -876,14 +989,9 @@ template <int MODE, int NMAX>
 cudaError_t occupancy_one(int *blocks)
 {
     using T = Traits<MODE, NMAX>;
-    const size_t dyn = T::SMEM_ACC ? (size_t)T::NACC * T::BLOCK * sizeof(float) : 0;
-    if (dyn > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(nr_mixed_kernel<MODE, NMAX>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, nr_mixed_kernel<MODE, NMAX>, T::BLOCK,
-                                                         dyn);
+    cudaError_t e = set_smem_attr<MODE, NMAX>();
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, nr_mixed_kernel<MODE, NMAX>, T::BLOCK, T::DYN);
 }
 
 #define NR_GRAD_BUCKETS(X) X(1) X(2) X(4) X(8) X(12) X(16) X(20) X(32) X(64)
@@ -903,13 +1011,20 @@ bool mixed_bucket_ok(int mode, int nmax)
 
 int mixed_block_threads(int mode, int nmax)
 {
-    return mode != kGrad ? 256 : nmax >= 32 ? 128 : 256;
+    if (mode != kGrad) return Traits<kModel, 1>::BLOCK;
+#define X(B) if (nmax == B) return Traits<kGrad, B>::BLOCK;
+    NR_GRAD_BUCKETS(X)
+#undef X
+    return 0;
 }
 
 size_t mixed_dyn_smem(int mode, int nmax)
 {
-    if (mode != kGrad || nmax < 8) return 0;
-    return (size_t)(4 * nmax + 3) * mixed_block_threads(mode, nmax) * sizeof(float);
+    if (mode != kGrad) return 0;
+#define X(B) if (nmax == B) return Traits<kGrad, B>::DYN;
+    NR_GRAD_BUCKETS(X)
+#undef X
+    return 0;
 }
 
 cudaError_t mixed_occupancy(int mode, int nmax, int *blocks)

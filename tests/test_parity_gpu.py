@@ -198,13 +198,13 @@ def test_deep_stacks_every_bucket():
 
 def test_stacks_deeper_than_the_workloads():
     """21..64 layers (beyond every workload): the FP32 recursion error grows
-    with depth, so the model bound scales as 1e-5 * n / 20 there."""
+    with depth, so the model and loglik bounds scale as 1e-5 * n / 20 there."""
     rng = np.random.default_rng(4)
     grid = (W.log_grid(77, 0.005, 0.25), 0.05 * W.log_grid(77, 0.005, 0.25))
     ns = [21, 33, 64]
     stacks = [(n, rand_stack(rng, n, d_range=(5, 60)), 0) for n in ns]
     wl = custom_workload(stacks, [grid])
-    assert_parity(wl, run_gpu(wl), run_oracle(wl), tol_m=TOL_M * 64 / 20)
+    assert_parity(wl, run_gpu(wl), run_oracle(wl), tol_m=TOL_M * 64 / 20, tol_ll=TOL_LL * 64 / 20)
 
 
 def test_empty_and_ragged_datasets():
