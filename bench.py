@@ -149,21 +149,48 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _traffic_from_profile(kernel_src: str, profile_txt: str):
-    """DRAM bytes per launch recorded with ncu for the current kernel source,
-    or None when the source changed since the capture."""
+def kernel_source_hash() -> str:
+    src = os.path.join(ROOT, "paper_2509_06924_gb300", "csrc", "nr_mixed.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def profile_record(workload: str) -> dict:
+    """Figures of the committed ncu summary of the gradient kernel on this
+    workload, or {} when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"nr_mixed_grad_{workload}.txt")
+    rec = {}
     try:
-        want = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-        rec = {}
-        for line in open(profile_txt):
-            if ":" in line:
+        for line in open(path):
+            if ":" in line and not line.startswith(" "):
                 k, v = line.split(":", 1)
                 rec[k.strip()] = v.strip()
-        if rec.get("kernel source sha256[:16]") != want:
-            return None
-        return float(rec["dram bytes per full launch"])
-    except (OSError, KeyError, ValueError):
-        return None
+    except OSError:
+        return {}
+    return rec if rec.get("kernel source sha256[:16]") == kernel_source_hash() else {}
+
+
+def fp64_fd_baseline(wl, stacks: int = 1024) -> dict:
+    """The plain FP64 GPU path with central-difference gradients (2P + 1
+    forward evaluations per stack) on the first `stacks` stacks."""
+    import torch
+    import paper_2509_06924_gb300 as nr
+    sub = wl.subset(np.arange(min(stacks, wl.n_stacks)))
+    ctx = nr.Context(n_quad=sub.n_quad, precision="fp64")
+    b = nr.Batch.from_workload(sub)
+    ctx.plan(b)
+    ctx.loglik_grad(b)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    reps = 2
+    for _ in range(reps):
+        ctx.loglik_grad(b)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ctx.close()
+    return {"value": sub.evals / (ms * 1e-3), "unit": UNIT, "sample": f"first {sub.n_stacks} stacks",
+            "ms_per_call": ms}
 
 
 def cpu_baseline(wl, target_s: float = 10.0) -> dict:
@@ -319,8 +346,8 @@ def run_ours(args):
     kernel_ms = ms  # the step is one launch of the gradient kernel per layer bucket
     achieved = flops / (kernel_ms * 1e-3) / 1e12
     peak = peak_fp32_tflops()
-    traffic = _traffic_from_profile(os.path.join(ROOT, "paper_2509_06924_gb300", "csrc", "nr_mixed.cu"),
-                                    os.path.join(ROOT, "profiles", f"nr_mixed_grad_{args.workload}.txt"))
+    prof = profile_record(args.workload)
+    traffic = float(prof["dram bytes per full launch"]) if "dram bytes per full launch" in prof else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -333,10 +360,19 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)"},
         "e2e": e2e,
+        "fp64_fd_baseline": None if args.no_cpu_baseline else fp64_fd_baseline(wl),
         "gpu_launches": int(info["launches"]) * args.steps,
         "clocks": clk.summary(),
         "wall_s_timed_region": t_wall,
     }
+    if line["fp64_fd_baseline"]:
+        line["fp64_fd_baseline"]["speedup"] = value / ws / line["fp64_fd_baseline"]["value"]
+    if "fp32 inst per eval" in prof:
+        ipe = float(prof["fp32 inst per eval"])
+        peak_inst = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+        line["fp32_issue"] = {"inst_per_eval": ipe, "achieved": value / ws * ipe / 1e12, "peak": peak_inst,
+                              "unit": "T inst/s", "frac": value / ws * ipe / 1e12 / peak_inst,
+                              "basis": "FP32 FFMA/FADD/FMUL per evaluation counted by ncu"}
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)

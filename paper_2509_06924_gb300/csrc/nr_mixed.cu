@@ -896,16 +896,21 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 }
                 __syncthreads();
             }
-            {   // loglik, d/dscale, d/dbkg live in the kn == 0 lanes
-                double a0 = (double)ll_hi + (double)ll_lo, a1 = gsc_acc, a2 = gbk_acc;
+            {   // loglik (float pair), d/dscale, d/dbkg live in the kn == 0 lanes;
+                // warp sums stay on the FP32 pipe, FP64 only across warps
+                float h = ll_hi, l = ll_lo, a1 = gsc_acc, a2 = gbk_acc;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    a0 += __shfl_xor_sync(kFull, a0, o);
+                    const float h2 = __shfl_xor_sync(kFull, h, o), l2 = __shfl_xor_sync(kFull, l, o);
+                    float s, e;
+                    two_sum(h, h2, s, e);
+                    h = s;
+                    l = __fadd_rn(__fadd_rn(l, l2), e);
                     a1 += __shfl_xor_sync(kFull, a1, o);
                     a2 += __shfl_xor_sync(kFull, a2, o);
                 }
                 if (lane == 0) {
-                    sh_redd[warp][0] = a0;
+                    sh_redd[warp][0] = (double)h + (double)l;
                     sh_redd[warp][1] = a1;
                     sh_redd[warp][2] = a2;
                 }
