@@ -166,6 +166,40 @@ nr_status nr_quadrature(int32_t K, double *x, double *w);
 nr_status nr_plan_info(nr_ctx *ctx, const nr_batch *batch, int64_t *evals, int32_t *tile_q,
                        int32_t *chunk_q, int32_t *grid_ctas, int32_t *launches);
 
+/* ------------------------------------------------------------------------
+ * nr_loglik_grad_noalloc -- log-likelihood and gradient without allocating.
+ * The paper has no counterpart: this entry point exists for callers that are
+ * not allowed to allocate device memory (a plug-in whose host application
+ * owns every allocation through its own pool, a real-time loop that must not
+ * enter the driver's allocator, a process that has reserved the GPU's memory
+ * up front).  It needs no context and no plan and calls no cudaMalloc or
+ * cudaFree: its work list, queue tickets and status word live in one fixed
+ * device array of the library (about 1 MiB, held by every GPU that loads the
+ * library until the process exits).
+ *
+ *   batch:        as for nr_loglik_grad, DEVICE memory only
+ *                 (batch->memory == NR_MEM_DEVICE), at most
+ *                 NR_NOALLOC_MAX_STACKS stacks; r_obs and r_err required.
+ *   n_quad:       quadrature nodes K in [1, NR_MAX_QUAD].
+ *   loglik, grad: device outputs as for nr_loglik_grad (either may be NULL).
+ *   device_flags: optional device int32; cleared, then given the NR_FLAG_*
+ *                 bits this call raised (NULL: flags are not reported).
+ *   stream:       cudaStream_t; the call is asynchronous on it.
+ * Returns NR_EINVAL (with a message in nr_last_error) for more than
+ * NR_NOALLOC_MAX_STACKS stacks, host-memory batches or bad metadata,
+ * NR_ECUDA if a runtime call fails.
+ * The first call on a device looks up the array's device address with that
+ * device current; make it before any stream capture.  Every call shares the
+ * one array and leaves its contents behind (the call clears what must start
+ * at zero), so calls that overlap on the GPU (e.g. on two streams) race:
+ * issue them on one stream.  Results equal nr_loglik_grad's up to rounding
+ * (bitwise when nr_loglik_grad keeps whole stacks in one work item).
+ * ---------------------------------------------------------------------- */
+#define NR_NOALLOC_MAX_STACKS 16384
+
+nr_status nr_loglik_grad_noalloc(const nr_batch *batch, int32_t n_quad, double *loglik, double *grad,
+                                 int32_t *device_flags, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

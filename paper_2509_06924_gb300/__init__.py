@@ -33,7 +33,8 @@ NR_FLAG_NONFINITE_PARAM, NR_FLAG_BAD_Q, NR_FLAG_BAD_ERR = 1, 2, 4
 MAX_LAYERS = 64
 MAX_QUAD = 32
 EXPORTS = ("nr_create", "nr_destroy", "nr_last_error", "nr_plan", "nr_reflectivity", "nr_loglik",
-           "nr_loglik_grad", "nr_device_status", "nr_quadrature", "nr_plan_info")
+           "nr_loglik_grad", "nr_device_status", "nr_quadrature", "nr_plan_info", "nr_loglik_grad_noalloc")
+NOALLOC_MAX_STACKS = 16384
 
 
 class NRError(RuntimeError):
@@ -91,6 +92,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             lib.nr_device_status.argtypes = [vp, vp, i32p]
             lib.nr_quadrature.argtypes = [i32, dp, dp]
             lib.nr_plan_info.argtypes = [vp, ctypes.POINTER(CBatch), i64p, i32p, i32p, i32p, i32p]
+            lib.nr_loglik_grad_noalloc.argtypes = [ctypes.POINTER(CBatch), i32, vp, vp, vp, vp]
             for name in EXPORTS:
                 if name not in ("nr_destroy", "nr_last_error"):
                     getattr(lib, name).restype = ctypes.c_int
@@ -276,6 +278,17 @@ class Context:
         if st not in (NR_OK, NR_ENONFINITE):
             _check(st)
         return int(f.value)
+
+
+def loglik_grad_noalloc(batch: Batch, n_quad: int, ll_out, grad_out, flags_out=None, stream=None) -> None:
+    """Log-likelihood and gradient through nr_loglik_grad_noalloc, for hosts
+    that may not allocate device memory: the caller passes device outputs
+    (and optionally a device int32 for the error flags); the library
+    allocates nothing."""
+    cb = batch._c()
+    _check(load_library().nr_loglik_grad_noalloc(
+        ctypes.byref(cb), n_quad, ctypes.c_void_p(ll_out.data_ptr()), ctypes.c_void_p(grad_out.data_ptr()),
+        ctypes.c_void_p(flags_out.data_ptr() if flags_out is not None else None), _stream_handle(stream)))
 
 
 def _autograd_function():

@@ -185,6 +185,11 @@ uint64_t fnv(uint64_t h, const void *data, size_t n)
 
 } // namespace
 
+namespace nrimpl {
+// Message for nr_last_error() from the other translation units.
+void record_error(const char *msg) { g_last_error = msg; }
+} // namespace nrimpl
+
 struct nr_ctx {
     int device = 0;
     int sms = 0;
