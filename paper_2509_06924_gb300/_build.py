@@ -50,9 +50,13 @@ def _run(cmd):
     return r
 
 
-def build(force: bool = False, verbose: bool = False, defines=None, out: str | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, defines=None, out: str | None = None,
+          csrc: str | None = None, include: str | None = None) -> str:
     """Compile (if needed) and return the path of libnr.so.  `defines`
-    (e.g. {"NR_MINB_GRAD1": 3}) and `out` build a variant library elsewhere."""
+    (e.g. {"NR_MINB_GRAD1": 3}), `out` and a source tree (`csrc`,
+    `include`) build a variant library elsewhere."""
+    CSRC_ = csrc or CSRC
+    INCLUDE_ = include or INCLUDE
     lib_path = out or LIB
     if not force and out is None and not _stale():
         return LIB
@@ -60,20 +64,20 @@ def build(force: bool = False, verbose: bool = False, defines=None, out: str | N
     os.makedirs(out_dir, exist_ok=True)
     dflags = [f"-D{k}={v}" for k, v in (defines or {}).items()]
     nvcc = _nvcc()
-    inc = ["-I", INCLUDE, "-I", CSRC]
+    inc = ["-I", INCLUDE_, "-I", CSRC_]
     jobs = []
     objs = []
     for src in CU_SOURCES:
         obj = os.path.join(out_dir, src + ".o")
         objs.append(obj)
         jobs.append([nvcc, "-std=c++17", *ARCH, "-O3", "-lineinfo", "-Xcompiler", "-fPIC", *dflags,
-                     "-Xptxas", "-v" if verbose else "-O3", *inc, "-c", os.path.join(CSRC, src), "-o", obj])
+                     "-Xptxas", "-v" if verbose else "-O3", *inc, "-c", os.path.join(CSRC_, src), "-o", obj])
     cuda_inc = os.path.join(_cuda_home(), "include")
     for src in CPP_SOURCES:
         obj = os.path.join(out_dir, src + ".o")
         objs.append(obj)
         jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", *inc, "-I", cuda_inc, "-c",
-                     os.path.join(CSRC, src), "-o", obj])
+                     os.path.join(CSRC_, src), "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         results = list(ex.map(_run, jobs))
     if verbose:

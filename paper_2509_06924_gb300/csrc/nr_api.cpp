@@ -294,7 +294,7 @@ nr_status build_worklist(nr_ctx *ctx, Plan &pl, int mode, WorkList &wl)
         g.nmax = b;
         g.tile_q = tile_for(ctx, mode, b);
         int occ = 0;
-        cudaError_t e = mixed_occupancy(mode, b, &occ);
+        cudaError_t e = mixed_occupancy(mode, b, ctx->qc.K, &occ);
         if (e != cudaSuccess) return fail(NR_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
         occ = std::max(occ, 1);
         const int64_t resident = (int64_t)ctx->sms * occ;

@@ -78,7 +78,7 @@ struct KernelArgs {
 // one layer); 0 selects the runtime-n forward kernel (model / loglik modes).
 int mixed_block_threads(int mode, int nmax);
 size_t mixed_dyn_smem(int mode, int nmax);
-cudaError_t mixed_occupancy(int mode, int nmax, int *blocks_per_sm);
+cudaError_t mixed_occupancy(int mode, int nmax, int K, int *blocks_per_sm);
 cudaError_t launch_mixed(int mode, int nmax, int grid, const KernelArgs &a, const QuadConst &qc,
                          cudaStream_t st);
 bool mixed_bucket_ok(int mode, int nmax);

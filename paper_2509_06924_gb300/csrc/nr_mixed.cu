@@ -159,14 +159,22 @@ __device__ __forceinline__ Kz kz_sqrt(float uh, float ul, float a)
 }
 
 // k of medium j >= 1 from k_0^2 = (p_hi + p_lo) and c_j = 4 pi (rho_j - rho_0).
+// Without REFINE (the backing medium: no phase) u is formed in FP32, where
+// p_hi - c_hi is exact near the critical edge (Sterbenz) and the low words
+// keep the rest to FP32 accuracy.
 template <bool REFINE>
 __device__ __forceinline__ Kz medium_kz(float p_hi, float p_lo, float2 c, float a)
 {
-    float uh, ul;
-    two_sum(p_hi, -c.x, uh, ul);
-    ul = __fadd_rn(ul, __fadd_rn(p_lo, -c.y));
-    fast_two_sum(uh, ul, uh, ul);
-    return kz_sqrt<REFINE>(uh, ul, a);
+    if constexpr (REFINE) {
+        float uh, ul;
+        two_sum(p_hi, -c.x, uh, ul);
+        ul = __fadd_rn(ul, __fadd_rn(p_lo, -c.y));
+        fast_two_sum(uh, ul, uh, ul);
+        return kz_sqrt<true>(uh, ul, a);
+    } else {
+        const float u = (p_hi - c.x) + (p_lo - c.y);
+        return kz_sqrt<false>(u, 0.f, a);
+    }
 }
 
 // E = exp(2 i k d).  The real phase 2 Re(k) d is formed in double-float and
@@ -454,7 +462,7 @@ __device__ void finalize_stack(const double *raw, int n, const double *p, int s,
 }
 
 // ---------------------------------------------------------------- kernel --
-template <int MODE, int NMAX>
+template <int MODE, int NMAX, int KC>
 __global__ void __launch_bounds__(Traits<MODE, NMAX>::BLOCK, Traits<MODE, NMAX>::MINB)
 nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
 {
@@ -481,7 +489,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int K = qc.K;
+    const int K = KC > 0 ? KC : qc.K; // KC: quadrature order fixed at compile time (0: runtime)
     const int KP = K;            // node stride of a Q slot in sh_wR
     const int TQ = ka.tile_q;
     const int qslot = tid / K;
@@ -624,7 +632,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             // a3-a6 forward, from the backing upwards
             Kz kst[T::STORE ? NM + 2 : 1];
             float2 rst[T::STORE ? NM + 1 : 1], Gst[T::STORE ? NM + 1 : 1];
-            float2 Est[T::STORE ? NM + 2 : 1], Dst[T::STORE ? NM + 1 : 1];
+            float2 Est[T::STORE ? NM + 2 : 1], Dst[T::STORE ? NM + 1 : 1], Yst[T::STORE ? NM + 1 : 1];
             float2 Xr[GRAD && T::UNROLL ? NM + 1 : 1];
             auto Xput = [&](int j, float2 v) __attribute__((always_inline)) {
                 if constexpr (GRAD) {
@@ -654,9 +662,10 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     if constexpr (T::STORE) kst[j + 1] = kbelow;
                 } else {
                     const float2 Ej = layer_phase(kbelow, sm.d[j + 1]);
+                    const float2 Yj = cmul(Xbelow, Ej);
                     float2 Dj;
-                    Xj = mobius(rj, cmul(Xbelow, Ej), Dj);
-                    if constexpr (T::STORE) { Est[j + 1] = Ej; Dst[j] = Dj; }
+                    Xj = mobius(rj, Yj, Dj);
+                    if constexpr (T::STORE) { Est[j + 1] = Ej; Dst[j] = Dj; Yst[j] = Yj; }
                 }
                 if constexpr (T::STORE) { kst[j] = kj; rst[j] = rj; Gst[j] = Gj; }
                 Xput(j, Xj);
@@ -748,7 +757,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         if constexpr (T::STORE) {
                             Ej1 = Est[j + 1];
                             Dj = Dst[j];
-                            Y = cmul(X1, Ej1);
+                            Y = Yst[j];
                         } else {
                             Ej1 = layer_phase(kj1, sm.d[j + 1]);
                             Y = cmul(X1, Ej1);
@@ -966,37 +975,60 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     }
 }
 
-template <int MODE, int NMAX>
+template <int MODE, int NMAX, int KC>
 cudaError_t set_smem_attr()
 {
     using T = Traits<MODE, NMAX>;
     if (T::DYN > 48 * 1024)
-        return cudaFuncSetAttribute(nr_mixed_kernel<MODE, NMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(nr_mixed_kernel<MODE, NMAX, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)T::DYN);
     return cudaSuccess;
 }
 
-template <int MODE, int NMAX>
-cudaError_t launch_one(int grid, const KernelArgs &a, const QuadConst &qc, cudaStream_t st)
+template <int MODE, int NMAX, int KC>
+cudaError_t launch_k(int grid, const KernelArgs &a, const QuadConst &qc, cudaStream_t st)
 {
     using T = Traits<MODE, NMAX>;
     static bool attr_done = false; // per process: the attribute belongs to the function
     if (!attr_done) {
-        cudaError_t e = set_smem_attr<MODE, NMAX>();
+        cudaError_t e = set_smem_attr<MODE, NMAX, KC>();
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    nr_mixed_kernel<MODE, NMAX><<<grid, T::BLOCK, T::DYN, st>>>(a, qc);
+    nr_mixed_kernel<MODE, NMAX, KC><<<grid, T::BLOCK, T::DYN, st>>>(a, qc);
     return cudaGetLastError();
 }
 
-template <int MODE, int NMAX>
-cudaError_t occupancy_one(int *blocks)
+template <int MODE, int NMAX, int KC>
+cudaError_t occupancy_k(int *blocks)
 {
     using T = Traits<MODE, NMAX>;
-    cudaError_t e = set_smem_attr<MODE, NMAX>();
+    cudaError_t e = set_smem_attr<MODE, NMAX, KC>();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, nr_mixed_kernel<MODE, NMAX>, T::BLOCK, T::DYN);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, nr_mixed_kernel<MODE, NMAX, KC>, T::BLOCK,
+                                                         T::DYN);
+}
+
+// The 1-layer kernels are also compiled for the workloads' quadrature orders
+// (17 and 21 nodes), which turns the per-tile index arithmetic into constants.
+template <int MODE, int NMAX>
+cudaError_t launch_one(int grid, int K, const KernelArgs &a, const QuadConst &qc, cudaStream_t st)
+{
+    if constexpr (NMAX == 1) {
+        if (K == 21) return launch_k<MODE, NMAX, 21>(grid, a, qc, st);
+        if (K == 17) return launch_k<MODE, NMAX, 17>(grid, a, qc, st);
+    }
+    return launch_k<MODE, NMAX, 0>(grid, a, qc, st);
+}
+
+template <int MODE, int NMAX>
+cudaError_t occupancy_one(int K, int *blocks)
+{
+    if constexpr (NMAX == 1) {
+        if (K == 21) return occupancy_k<MODE, NMAX, 21>(blocks);
+        if (K == 17) return occupancy_k<MODE, NMAX, 17>(blocks);
+    }
+    return occupancy_k<MODE, NMAX, 0>(blocks);
 }
 
 #define NR_GRAD_BUCKETS(X) X(1) X(2) X(4) X(8) X(12) X(16) X(20) X(32) X(64)
@@ -1032,15 +1064,15 @@ size_t mixed_dyn_smem(int mode, int nmax)
     return 0;
 }
 
-cudaError_t mixed_occupancy(int mode, int nmax, int *blocks)
+cudaError_t mixed_occupancy(int mode, int nmax, int K, int *blocks)
 {
     switch (mode) {
     case kModel:
-        return nmax == 1 ? occupancy_one<kModel, 1>(blocks) : occupancy_one<kModel, 0>(blocks);
+        return nmax == 1 ? occupancy_one<kModel, 1>(K, blocks) : occupancy_one<kModel, 0>(K, blocks);
     case kLoglik:
-        return nmax == 1 ? occupancy_one<kLoglik, 1>(blocks) : occupancy_one<kLoglik, 0>(blocks);
+        return nmax == 1 ? occupancy_one<kLoglik, 1>(K, blocks) : occupancy_one<kLoglik, 0>(K, blocks);
     default:
-#define X(B) if (nmax == B) return occupancy_one<kGrad, B>(blocks);
+#define X(B) if (nmax == B) return occupancy_one<kGrad, B>(K, blocks);
         NR_GRAD_BUCKETS(X)
 #undef X
     }
@@ -1050,14 +1082,15 @@ cudaError_t mixed_occupancy(int mode, int nmax, int *blocks)
 cudaError_t launch_mixed(int mode, int nmax, int grid, const KernelArgs &a, const QuadConst &qc,
                          cudaStream_t st)
 {
+    const int K = qc.K;
     switch (mode) {
     case kModel:
-        return nmax == 1 ? launch_one<kModel, 1>(grid, a, qc, st) : launch_one<kModel, 0>(grid, a, qc, st);
+        return nmax == 1 ? launch_one<kModel, 1>(grid, K, a, qc, st) : launch_one<kModel, 0>(grid, K, a, qc, st);
     case kLoglik:
-        return nmax == 1 ? launch_one<kLoglik, 1>(grid, a, qc, st)
-                         : launch_one<kLoglik, 0>(grid, a, qc, st);
+        return nmax == 1 ? launch_one<kLoglik, 1>(grid, K, a, qc, st)
+                         : launch_one<kLoglik, 0>(grid, K, a, qc, st);
     default:
-#define X(B) if (nmax == B) return launch_one<kGrad, B>(grid, a, qc, st);
+#define X(B) if (nmax == B) return launch_one<kGrad, B>(grid, K, a, qc, st);
         NR_GRAD_BUCKETS(X)
 #undef X
     }

@@ -237,7 +237,7 @@ extern "C" nr_status nr_loglik_grad_noalloc(const nr_batch *b, int32_t n_quad, d
         const int nmax = kBuckets[g];
         const int block = mixed_block_threads(kGrad, nmax);
         int occ = 1;
-        if (mixed_occupancy(kGrad, nmax, &occ) != cudaSuccess) return err(NR_ECUDA, "occupancy query failed");
+        if (mixed_occupancy(kGrad, nmax, n_quad, &occ) != cudaSuccess) return err(NR_ECUDA, "occupancy query failed");
         a.items = d_items + first;
         a.n_items = count[g];
         a.tile_q = std::max(1, std::min(block / n_quad, block / kSubLanes));
