@@ -54,10 +54,27 @@ constexpr float kEdgeFrac = NR_EDGE_FRAC;
 // CTAs per SM the compiler is asked to fit (register cap) for the 1-layer
 // gradient bucket and the forward kernels; overridable at build time.
 #ifndef NR_MINB_GRAD1
-#define NR_MINB_GRAD1 4
+#define NR_MINB_GRAD1 6
 #endif
 #ifndef NR_MINB_FWD
 #define NR_MINB_FWD 4
+#endif
+// threads per CTA and CTAs per SM of the 1-layer forward (model / loglik)
+// kernel; the rolled forward kernel keeps 256 threads and NR_MINB_FWD
+#ifndef NR_BLOCK_FWD1
+#define NR_BLOCK_FWD1 128
+#endif
+#ifndef NR_MINB_FWD1
+#define NR_MINB_FWD1 8
+#endif
+// threads per CTA of the 1-layer gradient kernel
+#ifndef NR_BLOCK_GRAD1
+#define NR_BLOCK_GRAD1 128
+#endif
+// 1: Nevot-Croce phase and |u + i a| are computed without data-dependent
+// branches (a few more XU operations, straight-line code)
+#ifndef NR_BRANCHFREE
+#define NR_BRANCHFREE 1
 #endif
 // 1: the 1-layer kernels treat n as the compile-time constant 1
 #ifndef NR_EXACT1
@@ -131,7 +148,7 @@ __device__ __forceinline__ Kz kz_sqrt(float uh, float ul, float a)
 {
     const float au = fabsf(uh);
     float m = au;
-    if (a != 0.f) {
+    if (NR_BRANCHFREE || a != 0.f) {
         const float m2 = fmaf(uh, uh, a * a);
         m = m2 * rsqrt_approx(fmaxf(m2, 1e-37f));
     }
@@ -210,7 +227,7 @@ __device__ __forceinline__ float2 fresnel_nc(float2 ka, float2 kb, float2 N, flo
     const float amp = __expf(s * kk.x);
     float2 F = make_float2(amp, 0.f);
     const float wi = s * kk.y;
-    if (wi != 0.f) {
+    if (NR_BRANCHFREE || wi != 0.f) {
         float sn, cs;
         __sincosf(wi, &sn, &cs);
         F = make_float2(amp * cs, amp * sn);
@@ -349,7 +366,7 @@ struct Traits {
     static constexpr int NM = NMAX > 0 ? NMAX : NR_MAX_LAYERS; // smem capacity
     // deep gradient buckets run 128-thread CTAs so that their per-thread
     // state in shared memory still leaves room for several CTAs per SM
-    static constexpr int BLOCK = !kGradMode ? 256 : NMAX >= 16 ? 128 : 256;
+    static constexpr int BLOCK = !kGradMode ? (NMAX == 1 ? NR_BLOCK_FWD1 : 256) : NMAX == 1 ? NR_BLOCK_GRAD1 : NMAX >= 16 ? 128 : 256;
     static constexpr bool STORE = kGradMode && NMAX <= 2;     // keep all intermediates
     static constexpr bool UNROLL = NMAX >= 1 && NMAX <= 4;    // register arrays, unrolled sweeps
     static constexpr bool SMEM_ACC = kGradMode && !UNROLL;    // partials in shared memory
@@ -364,7 +381,7 @@ struct Traits {
 #define NR_DEEP_REGS 96
 #endif
     // register caps: rolled deep kernels are held to NR_DEEP_REGS per thread
-    static constexpr int MINB = !kGradMode ? NR_MINB_FWD : NMAX == 1 ? NR_MINB_GRAD1 : NMAX <= 4 ? 3
+    static constexpr int MINB = !kGradMode ? (NMAX == 1 ? NR_MINB_FWD1 : NR_MINB_FWD) : NMAX == 1 ? NR_MINB_GRAD1 : NMAX <= 4 ? 3
                                 : 65536 / (BLOCK * NR_DEEP_REGS);
     static constexpr size_t DYN = (SMEM_ACC ? (size_t)NACC * BLOCK * 4 : 0) +
                                   (X_SMEM ? (size_t)(NM + 1) * BLOCK * 8 : 0);
@@ -1048,7 +1065,7 @@ bool mixed_bucket_ok(int mode, int nmax)
 
 int mixed_block_threads(int mode, int nmax)
 {
-    if (mode != kGrad) return Traits<kModel, 1>::BLOCK;
+    if (mode != kGrad) return nmax == 1 ? Traits<kModel, 1>::BLOCK : Traits<kModel, 0>::BLOCK;
 #define X(B) if (nmax == B) return Traits<kGrad, B>::BLOCK;
     NR_GRAD_BUCKETS(X)
 #undef X
