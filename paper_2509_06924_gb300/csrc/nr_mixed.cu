@@ -42,6 +42,7 @@ constexpr float kTwoPiHi = 6.28318548202514648438f;      // float(2 pi)
 constexpr float kTwoPiLo = -1.74845553146951715e-07f;    // 2 pi - kTwoPiHi
 constexpr float kRoundMagic = 12582912.0f;               // 1.5 * 2^23: x + M - M rounds x to an integer
 constexpr double kFourPiD = 12.566370614359172953850573533118;
+constexpr double kLog2ED = 1.4426950408889634073599246810019; // log2(e)
 constexpr float kLog2Pi = 1.83787706640934548356f;       // ln(2 pi)
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -88,6 +89,14 @@ __device__ __forceinline__ float rcp_approx(float x)
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+// 2^x; exp(y) is taken as 2^(y log2 e) with log2 e folded into the staged
+// per-stack constants
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ float rsqrt_approx(float x)
 {
     float r;
@@ -126,6 +135,11 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // Re(conj(a) * b)
 __device__ __forceinline__ float redot(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
+// conj(a) * b + c, four fused multiply-adds
+__device__ __forceinline__ float2 cfmac(float2 a, float2 b, float2 c)
+{
+    return make_float2(fmaf(a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
 __device__ __forceinline__ float2 cdiv(float2 a, float2 b)
 {
     const float inv = rcp_approx(fmaf(b.x, b.x, b.y * b.y));
@@ -197,34 +211,37 @@ __device__ __forceinline__ Kz medium_kz(float p_hi, float p_lo, float2 c, float 
 // E = exp(2 i k d).  The real phase 2 Re(k) d is formed in double-float and
 // reduced modulo 2 pi (Cody-Waite, two-word 2 pi; the multiple of 2 pi is
 // rounded with the 1.5 * 2^23 addition) before the FP32 sincos.
-__device__ __forceinline__ float2 layer_phase(const Kz &k, float2 d)
+// d2 = 2 d as (hi, lo); ea = -2 d log2(e), so |E| = 2^(Im(k) ea).
+__device__ __forceinline__ float2 layer_phase(const Kz &k, float2 d2, float ea)
 {
-    const float t = 2.f * k.re, tl = 2.f * k.lo;
-    const float ph = __fmul_rn(t, d.x);
-    float pl = fmaf(t, d.x, -ph);
-    pl = fmaf(t, d.y, pl);
-    pl = fmaf(tl, d.x, pl);
+    const float t = k.re, tl = k.lo;
+    const float ph = __fmul_rn(t, d2.x);
+    float pl = fmaf(t, d2.x, -ph);
+    pl = fmaf(t, d2.y, pl);
+    pl = fmaf(tl, d2.x, pl);
     const float nt = __fadd_rn(fmaf(ph, kInv2Pi, kRoundMagic), -kRoundMagic);
     float red = fmaf(-nt, kTwoPiHi, ph);
     red = fmaf(-nt, kTwoPiLo, red);
     red += pl;
     float s, c;
     __sincosf(red, &s, &c);
-    const float amp = __expf(-2.f * k.im * d.x);
+    const float amp = ex2_approx(k.im * ea);
     return make_float2(amp * c, amp * s);
 }
 
 // r_j with Nevot-Croce roughness; also returns G = exp(s k_a k_b) / S^2 with
-// S = k_a + k_b (the adjoint needs it): r = N G.
-__device__ __forceinline__ float2 fresnel_nc(float2 ka, float2 kb, float2 N, float s, float2 &G)
+// S = k_a + k_b (the adjoint needs it): r = N G.  sl = s log2(e).  REAL_A:
+// k_a is real (the fronting medium), its imaginary part is not read.
+template <bool REAL_A>
+__device__ __forceinline__ float2 fresnel_nc(float2 ka, float2 kb, float2 N, float s, float sl, float2 &G)
 {
-    const float Sx = ka.x + kb.x, Sy = ka.y + kb.y;
+    const float Sx = ka.x + kb.x, Sy = REAL_A ? kb.y : ka.y + kb.y;
     const float n2 = fmaf(Sx, Sx, Sy * Sy);
     const float inv = n2 > 0.f ? rcp_approx(n2) : 0.f;
     const float2 iS = make_float2(Sx * inv, -Sy * inv); // 1/S
     const float2 iS2 = csqr(iS);                         // 1/S^2
-    const float2 kk = cmul(ka, kb);
-    const float amp = __expf(s * kk.x);
+    const float2 kk = REAL_A ? make_float2(ka.x * kb.x, ka.x * kb.y) : cmul(ka, kb);
+    const float amp = ex2_approx(sl * kk.x);
     float2 F = make_float2(amp, 0.f);
     const float wi = s * kk.y;
     if (NR_BRANCHFREE || wi != 0.f) {
@@ -343,15 +360,15 @@ __device__ __forceinline__ float2 edge_ubar(float2 a, float2 k, float2 b, float 
 // Drains `cnt` queued interior-edge entries of one warp (one per lane) into
 // per-thread partials kept in shared memory (acc points at this thread's
 // slot of medium 1's Re-accumulator; stride between accumulators `stride`,
-// Re -> Im distance `im_off`).  Kept out of line so that the rolled sweep
-// it is called from keeps its register budget.
+// Re -> Im distance `im_off`; d2: twice the layer thicknesses).  Kept out of
+// line so that the rolled sweep it is called from keeps its register budget.
 template <int EQ>
-__device__ __noinline__ void eq_drain_smem(float2 (*q)[EQ], const int *qj, const float *sg, const float2 *dd, int n,
+__device__ __noinline__ void eq_drain_smem(float2 (*q)[EQ], const int *qj, const float *sg, const float2 *d2, int n,
                                            int lane, int cnt, float *acc, int stride, int im_off)
 {
     if (lane < cnt) {
         const int j = qj[lane];
-        const float2 ub = edge_ubar(q[0][lane], q[1][lane], q[2][lane], sg[j - 1], sg[j], dd[j].x, q[3][lane],
+        const float2 ub = edge_ubar(q[0][lane], q[1][lane], q[2][lane], sg[j - 1], sg[j], 0.5f * d2[j].x, q[3][lane],
                                     j == n, q[4][lane]);
         // conj(kbar)/k_j = 2 conj(ubar)
         acc[(j - 1) * stride] += 2.f * ub.x;
@@ -383,6 +400,9 @@ struct Traits {
     // register caps: rolled deep kernels are held to NR_DEEP_REGS per thread
     static constexpr int MINB = !kGradMode ? (NMAX == 1 ? NR_MINB_FWD1 : NR_MINB_FWD) : NMAX == 1 ? NR_MINB_GRAD1 : NMAX <= 4 ? 3
                                 : 65536 / (BLOCK * NR_DEEP_REGS);
+    // Q points staged in shared memory per super-tile (several tiles)
+    static constexpr int CAPQ = SMEM_ACC ? 96 : 256;
+    static_assert(CAPQ >= BLOCK / kSubLanes, "a super-tile holds at least one tile");
     static constexpr size_t DYN = (SMEM_ACC ? (size_t)NACC * BLOCK * 4 : 0) +
                                   (X_SMEM ? (size_t)(NM + 1) * BLOCK * 8 : 0);
 };
@@ -394,8 +414,10 @@ struct StackSmem {
     float a[NM + 2];   // 4 pi iota_j, j = 1..n+1
     float2 N[NM + 1];  // 4 pi (rho_{j+1} - rho_j) + 4 pi i (iota_j - iota_{j+1})
     float s[NM + 1];   // -2 sigma_j^2
+    float sl[NM + 1];  // -2 sigma_j^2 log2(e)
     float sg[NM + 1];  // sigma_j
-    float2 d[NM + 2];  // thickness (hi, lo), j = 1..n
+    float2 d2[NM + 2]; // twice the thickness (hi, lo), j = 1..n
+    float ea[NM + 2];  // -2 d_j log2(e)
     float scale, bkg;
 };
 
@@ -421,7 +443,8 @@ __device__ void stage_stack(StackSmem<NM> &sm, const double *p, int n, int tid, 
             bad |= !isfinite(rj) || !isfinite(ij);
             if (j <= n) {
                 const double dj = p[j - 1];
-                sm.d[j] = split_double(dj);
+                sm.d2[j] = split_double(2.0 * dj);
+                sm.ea[j] = (float)(-2.0 * kLog2ED * dj);
                 bad |= !isfinite(dj);
             }
         } else {
@@ -434,6 +457,7 @@ __device__ void stage_stack(StackSmem<NM> &sm, const double *p, int n, int tid, 
             sm.N[j] = make_float2((float)(kFourPiD * (p[n + j + 1] - p[n + j])),
                                   (float)(kFourPiD * (iot_j - iot_j1)));
             sm.s[j] = (float)(-2.0 * sig * sig);
+            sm.sl[j] = (float)(-2.0 * kLog2ED * sig * sig);
             sm.sg[j] = (float)sig;
             bad |= !isfinite(sig);
         }
@@ -492,6 +516,10 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
 
     __shared__ StackSmem<NM> sm;
     __shared__ float sh_wR[2][2 * BLOCK]; // w_k R per (Q slot, node), double-buffered
+    // the super-tile's data per Q point: (Q, dQ, R_obs, 1/err), and the
+    // (residual, smeared R) pairs its tiles leave for the likelihood sums
+    __shared__ float4 sh_qd[T::CAPQ];
+    __shared__ float2 sh_rs[LIK ? T::CAPQ : 1];
     __shared__ double sh_red[T::WARPS][32];
     __shared__ double sh_redd[T::WARPS][4];
     __shared__ double sh_raw[T::NRAW];
@@ -553,6 +581,17 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 else accr[idx] += v;
             }
         };
+        // acc[idx] += a b + c d, fused into the accumulator
+        auto acc_fma2 = [&](int idx, float a, float b, float c, float d) __attribute__((always_inline)) {
+            if constexpr (GRAD) {
+                if constexpr (T::SMEM_ACC) {
+                    float *ap = sh_acc + idx * BLOCK + tid;
+                    *ap = fmaf(a, b, fmaf(c, d, *ap));
+                } else {
+                    accr[idx] = fmaf(a, b, fmaf(c, d, accr[idx]));
+                }
+            }
+        };
         // medium j (runtime) -> its u accumulators
         auto acc_u = [&](int j, float2 v) __attribute__((always_inline)) {
             if constexpr (GRAD) {
@@ -573,12 +612,12 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
         // drain `cnt` <= 32 queued entries, one per lane, then shift the rest down
         auto eq_drain = [&](int cnt) {
             if constexpr (T::SMEM_ACC) {
-                eq_drain_smem<EQ>(sh_eq[warp], sh_eqj[warp], sm.sg, sm.d, n, lane, cnt, sh_acc + oUr * BLOCK + tid,
+                eq_drain_smem<EQ>(sh_eq[warp], sh_eqj[warp], sm.sg, sm.d2, n, lane, cnt, sh_acc + oUr * BLOCK + tid,
                                   BLOCK, (oUi - oUr) * BLOCK);
             } else if (lane < cnt) {
                 const int j = sh_eqj[warp][lane];
                 const float2 ub = edge_ubar(sh_eq[warp][0][lane], sh_eq[warp][1][lane], sh_eq[warp][2][lane],
-                                            sm.sg[j - 1], sm.sg[j], sm.d[j].x, sh_eq[warp][3][lane], j == n,
+                                            sm.sg[j - 1], sm.sg[j], 0.5f * sm.d2[j].x, sh_eq[warp][3][lane], j == n,
                                             sh_eq[warp][4][lane]);
                 // conj(kbar)/k_j = 2 conj(ubar)
                 acc_u(j, make_float2(2.f * ub.x, -2.f * ub.y));
@@ -595,47 +634,76 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             eq_cnt = rest;
         };
 
-        // per-lane sums of the loglik terms (lanes kn == 0), d/dscale, d/dbkg
+        // per-thread sums of the loglik terms, d/dscale, d/dbkg
         float ll_hi = 0.f, ll_lo = 0.f, gsc_acc = 0.f, gbk_acc = 0.f;
 
-        // software pipeline: inputs of the next tile are loaded while the
-        // current one computes
+        // Q data are staged per super-tile (span Q points, a whole number of
+        // tiles) by all threads at once.  The tiles of a super-tile leave one
+        // (residual, S) pair per Q point in sh_rs; the likelihood terms of a
+        // super-tile are summed with full warps when the next one is staged
+        // (and after the last tile), not by one lane per Q point per tile.
         const float *qp = ka.q + si.q_begin, *dqp = ka.dq + si.q_begin;
         const float *rop = ka.r_obs + si.q_begin, *rep = ka.r_err + si.q_begin;
-        float Qn = 0.1f, dQn = 0.f, Ron = 0.f, Ren = 1.f;
-        {
-            const int qi = wi.q_lo + qslot;
-            if (lane_on && qi < wi.q_hi) {
-                Qn = __ldg(qp + qi);
-                dQn = __ldg(dqp + qi);
-                if (LIK) { Ron = __ldg(rop + qi); Ren = __ldg(rep + qi); }
+        const int span = (T::CAPQ / TQ) * TQ;
+        int sb = wi.q_lo;     // first Q point of the staged super-tile
+        int s_next = wi.q_lo; // first Q point of the next one
+        int s_cnt = 0;        // staged Q points whose pairs await summation
+        auto consume = [&](int i) __attribute__((always_inline)) {
+            if constexpr (LIK) {
+                const float2 rs = sh_rs[i];
+                const float Re = __ldg(rep + sb + i);
+                if (!(Re > 0.f)) atomicOr(ka.status, NR_FLAG_BAD_ERR);
+                float t1, t2;
+                two_sum(ll_hi, fmaf(rs.x, rs.x, kLog2Pi + 2.f * logf(Re)), t1, t2);
+                ll_hi = t1;
+                ll_lo += t2;
+                if constexpr (GRAD) {
+                    const float dldm = -(rs.x * sh_qd[i].w);
+                    gsc_acc = fmaf(dldm, rs.y, gsc_acc);
+                    gbk_acc += dldm;
+                }
             }
-        }
+        };
+        auto restage = [&](int q0) {
+            __syncthreads(); // the previous super-tile's reads and pairs are complete
+            for (int i = tid; i < span; i += BLOCK) {
+                if (i < s_cnt) consume(i);
+                const int qa = q0 + i;
+                float4 v = make_float4(0.1f, 0.f, 0.f, 1.f);
+                if (qa < wi.q_hi) {
+                    v.x = __ldg(qp + qa);
+                    v.y = __ldg(dqp + qa);
+                    if (LIK) {
+                        v.z = __ldg(rop + qa);
+                        v.w = rcp_approx(__ldg(rep + qa));
+                    }
+                }
+                sh_qd[i] = v;
+            }
+            sb = q0;
+            s_next = q0 + span;
+            s_cnt = min(span, wi.q_hi - q0);
+            __syncthreads();
+        };
         __syncthreads();
 
         const float scale = sm.scale, bkg = sm.bkg;
+        const float wks = wk * scale;
         int buf = 0;
         for (int q0 = wi.q_lo; q0 < wi.q_hi; q0 += TQ, buf ^= 1) {
+            if (q0 == s_next) restage(q0);
             const int qi = q0 + qslot;
+            const int si_q = q0 - sb + qslot; // this lane's super-tile entry
             const bool act = lane_on && qi < wi.q_hi;
-            const float Qv = Qn, dQv = dQn, Ro = Ron, Re = Ren;
-            {   // prefetch the next tile
-                const int q1 = q0 + TQ + qslot;
-                Qn = 0.1f; dQn = 0.f; Ron = 0.f; Ren = 1.f;
-                if (lane_on && q1 < wi.q_hi) {
-                    Qn = __ldg(qp + q1);
-                    dQn = __ldg(dqp + q1);
-                    if (LIK) { Ron = __ldg(rop + q1); Ren = __ldg(rep + q1); }
-                }
-            }
+            const float4 qd = lane_on ? sh_qd[si_q] : make_float4(0.1f, 0.f, 0.f, 1.f);
             // a1: node position in double-float, k_0 = q/2, k_0^2
             float qh, ql;
             {
-                const float th = __fmul_rn(dQv, g_hi);
-                float tl = fmaf(dQv, g_hi, -th);
-                tl = fmaf(dQv, g_lo, tl);
+                const float th = __fmul_rn(qd.y, g_hi);
+                float tl = fmaf(qd.y, g_hi, -th);
+                tl = fmaf(qd.y, g_lo, tl);
                 float s, e;
-                two_sum(Qv, th, s, e);
+                two_sum(qd.x, th, s, e);
                 e = __fadd_rn(e, tl);
                 fast_two_sum(s, e, qh, ql);
             }
@@ -672,13 +740,16 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     kj = medium_kz<true>(p_hi, p_lo, sm.c[j], sm.a[j]);
                 }
                 float2 Gj;
-                const float2 rj = fresnel_nc(kc(kj), kc(kbelow), sm.N[j], sm.s[j], Gj);
+                // k_0 is real: the unrolled sweeps use the real-k_a form there
+                const float2 rj = (T::UNROLL && j == 0)
+                                      ? fresnel_nc<true>(kc(kj), kc(kbelow), sm.N[j], sm.s[j], sm.sl[j], Gj)
+                                      : fresnel_nc<false>(kc(kj), kc(kbelow), sm.N[j], sm.s[j], sm.sl[j], Gj);
                 float2 Xj;
                 if (j == n) {
                     Xj = rj;
                     if constexpr (T::STORE) kst[j + 1] = kbelow;
                 } else {
-                    const float2 Ej = layer_phase(kbelow, sm.d[j + 1]);
+                    const float2 Ej = layer_phase(kbelow, sm.d2[j + 1], sm.ea[j + 1]);
                     const float2 Yj = cmul(Xbelow, Ej);
                     float2 Dj;
                     Xj = mobius(rj, Yj, Dj);
@@ -719,29 +790,13 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 for (int o = 1; o < sgl; o <<= 1) ps += __shfl_xor_sync(kFull, ps, o);
                 S = __shfl_sync(kFull, ps, ((qslot - qs0) * sgl) & 31);
             }
-            if (act && (GRAD || kn == 0)) {
+            if constexpr (MODE == kModel) {
+                if (act && kn == 0) ka.r_out[si.out_off + qi] = fmaf(scale, S, bkg);
+            } else {
                 const float m = fmaf(scale, S, bkg);
-                if constexpr (MODE == kModel) {
-                    ka.r_out[si.out_off + qi] = m;
-                } else {
-                    const float ie = rcp_approx(Re);
-                    const float res = (m - Ro) * ie;
-                    if (kn == 0) {
-                        if (!(Re > 0.f)) atomicOr(ka.status, NR_FLAG_BAD_ERR);
-                        float t1, t2;
-                        two_sum(ll_hi, fmaf(res, res, kLog2Pi + 2.f * logf(Re)), t1, t2);
-                        ll_hi = t1;
-                        ll_lo += t2;
-                    }
-                    if constexpr (GRAD) {
-                        const float dldm = -res * ie;
-                        if (kn == 0) {
-                            gsc_acc = fmaf(dldm, S, gsc_acc);
-                            gbk_acc += dldm;
-                        }
-                        Rb = wk * scale * dldm;
-                    }
-                }
+                const float res = (m - qd.z) * qd.w; // (m - R) / err
+                if (act && kn == 0) sh_rs[si_q] = make_float2(res, S);
+                if constexpr (GRAD) Rb = act ? wks * -(res * qd.w) : 0.f; // w_k scale dl/dm
             }
             if constexpr (GRAD) {
                 // a7: adjoint sweep from the fronting down to the backing
@@ -764,7 +819,9 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     } else {
                         kj1 = (j == n) ? medium_kz<false>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1])
                                        : medium_kz<true>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1]);
-                        rj = fresnel_nc(kc(kj), kc(kj1), sm.N[j], sm.s[j], Gj);
+                        rj = (T::UNROLL && j == 0)
+                                 ? fresnel_nc<true>(kc(kj), kc(kj1), sm.N[j], sm.s[j], sm.sl[j], Gj)
+                                 : fresnel_nc<false>(kc(kj), kc(kj1), sm.N[j], sm.s[j], sm.sl[j], Gj);
                     }
                     float2 kbar1 = make_float2(0.f, 0.f);
                     float2 rb;
@@ -776,7 +833,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                             Dj = Dst[j];
                             Y = Yst[j];
                         } else {
-                            Ej1 = layer_phase(kj1, sm.d[j + 1]);
+                            Ej1 = layer_phase(kj1, sm.d2[j + 1], sm.ea[j + 1]);
                             Y = cmul(X1, Ej1);
                             const float2 rY = cmul(rj, Y);
                             const float dx = 1.f + rY.x, dy = rY.y;
@@ -784,29 +841,43 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                             Dj = make_float2(dx * inv, -dy * inv);
                         }
                         Zj = Y;
-                        const float2 D2 = csqr(Dj);
                         const float2 one = make_float2(1.f, 0.f);
-                        const float2 dXdr = cmul(csub(one, csqr(Y)), D2);
-                        const float2 dXdY = cmul(csub(one, csqr(rj)), D2);
-                        rb = cmulc(dXdr, Xb);
-                        const float2 Yb = cmulc(dXdY, Xb);
-                        const float2 Eb = cmulc(X1, Yb);
-                        const float2 Xb1 = cmulc(Ej1, Yb);
-                        const float2 iE = make_float2(-Ej1.y, Ej1.x);
-                        acc_add(oD + j, redot(Eb, cmul(kc(kj1), iE)));           // d_{j+1}
-                        kbar1 = cscale(cmulc(iE, Eb), 2.f * sm.d[j + 1].x);
-                        Xb = Xb1;
+                        // dX/dr = (1 - Y^2) D^2, dX/dY = (1 - r^2) D^2: both
+                        // adjoints share V = conj(D^2) Xbar
+                        const float2 V = cmulc(csqr(Dj), Xb);
+                        rb = cmulc(csub(one, csqr(Y)), V);
+                        const float2 Yb = cmulc(csub(one, csqr(rj)), V);
+                        Xb = cmulc(Ej1, Yb);
+                        // Y = X_{j+1} E_{j+1}: dY/dd = 2 i k Y and dY/dk = 2 i d Y.
+                        // With U = conj(Y) Ybar the d_{j+1} sum takes
+                        // Re(k) Im(U) - Im(k) Re(U) (halved) and kbar_{j+1} = -2 i d U.
+                        const float2 U = cmulc(Y, Yb);
+                        acc_fma2(oD + j, kj1.re, U.y, -kj1.im, U.x);
+                        const float dd = sm.d2[j + 1].x;
+                        kbar1 = make_float2(dd * U.y, -dd * U.x);
                     } else {
                         rb = Xb;
                     }
-                    const float2 T1 = cscale(Gj, 2.f);
-                    const float2 T2 = cscale(rj, sm.s[j]);
-                    const float2 dr_dkj = cmul(kc(kj1), cadd(T1, T2));
-                    const float2 dr_dkj1 = cmul(kc(kj), csub(T2, T1));
-                    kbar1 = cadd(kbar1, cmulc(dr_dkj1, rb));
-                    acc_add(oS + j, redot(rb, cmul(rj, cmul(kc(kj), kc(kj1)))));
+                    // dr/dk_j = k_{j+1} P and dr/dk_{j+1} = k_j M with
+                    // P = 2G + s r, M = s r - 2G
+                    const float sj = sm.s[j];
+                    const float2 A = make_float2(sj * rj.x, sj * rj.y);
+                    const float2 P = make_float2(fmaf(2.f, Gj.x, A.x), fmaf(2.f, Gj.y, A.y));
+                    const float2 M = make_float2(fmaf(-2.f, Gj.x, A.x), fmaf(-2.f, Gj.y, A.y));
+                    const float2 H = cmulc(M, rb);               // kbar_{j+1} += conj(k_j) H
+                    const float2 rr = cmulc(rb, rj);             // accS += Re(rr k_j k_{j+1})
+                    const bool k_real = T::UNROLL && j == 0;     // k_0 is real
+                    float2 kk;
+                    if (k_real) {
+                        kbar1 = make_float2(fmaf(kj.re, H.x, kbar1.x), fmaf(kj.re, H.y, kbar1.y));
+                        kk = make_float2(kj.re * kj1.re, kj.re * kj1.im);
+                    } else {
+                        kbar1 = cfmac(kc(kj), H, kbar1);
+                        kk = cmul(kc(kj), kc(kj1));
+                    }
+                    acc_fma2(oS + j, rr.x, kk.x, -rr.y, kk.y);
                     if (j >= 1) {
-                        kbar = cadd(kbar, cmulc(dr_dkj, rb));
+                        kbar = cfmac(kc(kj1), cmulc(P, rb), kbar);
                         // k_j complete: accumulate conj(kbar) / k_j, or queue
                         // the interior-edge evaluation for this lane
                         const float m2 = fmaf(kj.re, kj.re, kj.im * kj.im);
@@ -831,10 +902,10 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                             }
                         }
                         if (!edge) {
-                            const float2 kk = cmul(kbar, kc(kj));
+                            const float2 kq = cmul(kbar, kc(kj));
                             const float inv = m2 > 0.f ? rcp_approx(m2) : 0.f;
-                            acc_add(oUr + j - 1, kk.x * inv);
-                            acc_add(oUi + j - 1, -kk.y * inv);
+                            acc_add(oUr + j - 1, kq.x * inv);
+                            acc_add(oUi + j - 1, -kq.y * inv);
                         }
                     }
                     Xb_up = Xb_in;
@@ -874,6 +945,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             }
             // ---- CTA reduction of the item's partial sums into sh_raw ----
             __syncthreads();
+            for (int i = tid; i < s_cnt; i += BLOCK) consume(i);
             if constexpr (GRAD && !T::SMEM_ACC) {
                 static_assert(T::NACC <= 32, "register partials exceed one reduction batch");
 #pragma unroll
