@@ -97,6 +97,11 @@ __device__ __forceinline__ float ex2_approx(float x)
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+__device__ __forceinline__ void sincos_approx(float x, float &sn, float &cs)
+{
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(sn) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cs) : "f"(x));
+}
 __device__ __forceinline__ float rsqrt_approx(float x)
 {
     float r;
@@ -135,6 +140,11 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 // Re(conj(a) * b)
 __device__ __forceinline__ float redot(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
+// 1 - a^2
+__device__ __forceinline__ float2 one_minus_sq(float2 a)
+{
+    return make_float2(fmaf(-a.x, a.x, fmaf(a.y, a.y, 1.f)), -2.f * a.x * a.y);
+}
 // conj(a) * b + c, four fused multiply-adds
 __device__ __forceinline__ float2 cfmac(float2 a, float2 b, float2 c)
 {
@@ -153,30 +163,31 @@ struct Kz {
 };
 __device__ __forceinline__ float2 kc(const Kz &k) { return make_float2(k.re, k.im); }
 
-// Principal sqrt of u + i a (u = uh + ul double-float, a >= 0) from one
-// rsqrt.  With REFINE, one Newton step on the dominant component makes Re k
-// good to double-float accuracy for propagating waves (a layer phase needs
-// it) and Im k good to FP32 accuracy for evanescent ones.
+// Principal sqrt of u + i a (u = uh + ul double-float, a >= 0; aa = (a, a^2))
+// from two rsqrt: t = sqrt((|u| + |z|) / 2) is the dominant component and
+// a / (2 t) the other.  With REFINE, one Newton step on the dominant
+// component makes Re k good to double-float accuracy for propagating waves
+// (a layer phase needs it) and Im k good to FP32 accuracy for evanescent ones.
 template <bool REFINE>
-__device__ __forceinline__ Kz kz_sqrt(float uh, float ul, float a)
+__device__ __forceinline__ Kz kz_sqrt(float uh, float ul, float2 aa)
 {
+    const float a = aa.x;
     const float au = fabsf(uh);
     float m = au;
     if (NR_BRANCHFREE || a != 0.f) {
-        const float m2 = fmaf(uh, uh, a * a);
+        const float m2 = fmaf(uh, uh, aa.y);
         m = m2 * rsqrt_approx(fmaxf(m2, 1e-37f));
     }
-    const float h = fmaxf(0.5f * (au + m), 1e-30f);
-    const float rt = rsqrt_approx(h);
-    const float t = h * rt;      // sqrt(h)
-    const float i2t = 0.5f * rt; // 1 / (2 sqrt(h))
+    // H = |u| + |z| = 2 t^2; rsqrt(2 H) = 1 / (2 t) exactly as 0.5 rsqrt(H / 2)
+    const float H = au + m;
+    const float i2t = rsqrt_approx(fmaxf(H + H, 4e-30f)); // 1 / (2 t)
+    const float t = H * i2t;
     const float small = a * i2t;
     const bool prop = uh >= 0.f;
     Kz k;
     if constexpr (REFINE) {
-        const float sgn = prop ? 1.f : -1.f;
         // residual of big^2 - small^2 = |u| and its Newton correction
-        const float e = fmaf(-t, t, sgn * uh) + fmaf(small, small, sgn * ul);
+        const float e = fmaf(-t, t, au) + fmaf(small, small, prop ? ul : -ul);
         const float corr = e * i2t;
         k.re = prop ? t : small;
         k.im = prop ? small : t + corr;
@@ -194,7 +205,7 @@ __device__ __forceinline__ Kz kz_sqrt(float uh, float ul, float a)
 // p_hi - c_hi is exact near the critical edge (Sterbenz) and the low words
 // keep the rest to FP32 accuracy.
 template <bool REFINE>
-__device__ __forceinline__ Kz medium_kz(float p_hi, float p_lo, float2 c, float a)
+__device__ __forceinline__ Kz medium_kz(float p_hi, float p_lo, float2 c, float2 a)
 {
     if constexpr (REFINE) {
         float uh, ul;
@@ -224,29 +235,30 @@ __device__ __forceinline__ float2 layer_phase(const Kz &k, float2 d2, float ea)
     red = fmaf(-nt, kTwoPiLo, red);
     red += pl;
     float s, c;
-    __sincosf(red, &s, &c);
+    sincos_approx(red, s, c);
     const float amp = ex2_approx(k.im * ea);
     return make_float2(amp * c, amp * s);
 }
 
 // r_j with Nevot-Croce roughness; also returns G = exp(s k_a k_b) / S^2 with
-// S = k_a + k_b (the adjoint needs it): r = N G.  sl = s log2(e).  REAL_A:
+// S = k_a + k_b (the adjoint needs it) and kk = k_a k_b: r = N G.  sl = s log2(e).  REAL_A:
 // k_a is real (the fronting medium), its imaginary part is not read.
 template <bool REAL_A>
-__device__ __forceinline__ float2 fresnel_nc(float2 ka, float2 kb, float2 N, float s, float sl, float2 &G)
+__device__ __forceinline__ float2 fresnel_nc(float2 ka, float2 kb, float2 N, float s, float sl, float2 &G,
+                                             float2 &kk)
 {
     const float Sx = ka.x + kb.x, Sy = REAL_A ? kb.y : ka.y + kb.y;
     const float n2 = fmaf(Sx, Sx, Sy * Sy);
     const float inv = n2 > 0.f ? rcp_approx(n2) : 0.f;
     const float2 iS = make_float2(Sx * inv, -Sy * inv); // 1/S
     const float2 iS2 = csqr(iS);                         // 1/S^2
-    const float2 kk = REAL_A ? make_float2(ka.x * kb.x, ka.x * kb.y) : cmul(ka, kb);
+    kk = REAL_A ? make_float2(ka.x * kb.x, ka.x * kb.y) : cmul(ka, kb);
     const float amp = ex2_approx(sl * kk.x);
     float2 F = make_float2(amp, 0.f);
     const float wi = s * kk.y;
     if (NR_BRANCHFREE || wi != 0.f) {
         float sn, cs;
-        __sincosf(wi, &sn, &cs);
+        sincos_approx(wi, sn, cs);
         F = make_float2(amp * cs, amp * sn);
     }
     G = cmul(F, iS2);
@@ -411,7 +423,7 @@ struct Traits {
 template <int NM>
 struct StackSmem {
     float2 c[NM + 2];  // 4 pi (rho_j - rho_0) as (hi, lo), j = 1..n+1
-    float a[NM + 2];   // 4 pi iota_j, j = 1..n+1
+    float2 a[NM + 2];  // 4 pi iota_j and its square, j = 1..n+1
     float2 N[NM + 1];  // 4 pi (rho_{j+1} - rho_j) + 4 pi i (iota_j - iota_{j+1})
     float s[NM + 1];   // -2 sigma_j^2
     float sl[NM + 1];  // -2 sigma_j^2 log2(e)
@@ -439,7 +451,7 @@ __device__ void stage_stack(StackSmem<NM> &sm, const double *p, int n, int tid, 
             const double rj = p[n + j];
             const double ij = p[2 * n + 2 + j - 1];
             sm.c[j] = split_double(kFourPiD * (rj - rho0));
-            sm.a[j] = (float)(kFourPiD * ij);
+            sm.a[j] = make_float2((float)(kFourPiD * ij), (float)(kFourPiD * kFourPiD * ij * ij));
             bad |= !isfinite(rj) || !isfinite(ij);
             if (j <= n) {
                 const double dj = p[j - 1];
@@ -516,7 +528,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
 
     __shared__ StackSmem<NM> sm;
     __shared__ float sh_wR[2][2 * BLOCK]; // w_k R per (Q slot, node), double-buffered
-    // the super-tile's data per Q point: (Q, dQ, R_obs, 1/err), and the
+    // the super-tile's data per Q point: (Q/2, dQ/2, R_obs, 1/err), and the
     // (residual, smeared R) pairs its tiles leave for the likelihood sums
     __shared__ float4 sh_qd[T::CAPQ];
     __shared__ float2 sh_rs[LIK ? T::CAPQ : 1];
@@ -638,7 +650,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
         float ll_hi = 0.f, ll_lo = 0.f, gsc_acc = 0.f, gbk_acc = 0.f;
 
         // Q data are staged per super-tile (span Q points, a whole number of
-        // tiles) by all threads at once.  The tiles of a super-tile leave one
+        // tiles) by all threads at once, as (Q/2, dQ/2, R_obs, 1/err).  The tiles of a super-tile leave one
         // (residual, S) pair per Q point in sh_rs; the likelihood terms of a
         // super-tile are summed with full warps when the next one is staged
         // (and after the last tile), not by one lane per Q point per tile.
@@ -669,10 +681,12 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             for (int i = tid; i < span; i += BLOCK) {
                 if (i < s_cnt) consume(i);
                 const int qa = q0 + i;
-                float4 v = make_float4(0.1f, 0.f, 0.f, 1.f);
+                // past the last Q point: a harmless node whose residual, and
+                // so adjoint seed, is 0 (1/err = 0)
+                float4 v = make_float4(0.05f, 0.f, 0.f, 0.f);
                 if (qa < wi.q_hi) {
-                    v.x = __ldg(qp + qa);
-                    v.y = __ldg(dqp + qa);
+                    v.x = 0.5f * __ldg(qp + qa);
+                    v.y = 0.5f * __ldg(dqp + qa);
                     if (LIK) {
                         v.z = __ldg(rop + qa);
                         v.w = rcp_approx(__ldg(rep + qa));
@@ -693,11 +707,14 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
         for (int q0 = wi.q_lo; q0 < wi.q_hi; q0 += TQ, buf ^= 1) {
             if (q0 == s_next) restage(q0);
             const int qi = q0 + qslot;
-            const int si_q = q0 - sb + qslot; // this lane's super-tile entry
+            // this lane's super-tile entry (idle lanes past the last Q slot
+            // read slot 0 and write nothing)
+            const int si_q = q0 - sb + (lane_on ? qslot : 0);
             const bool act = lane_on && qi < wi.q_hi;
-            const float4 qd = lane_on ? sh_qd[si_q] : make_float4(0.1f, 0.f, 0.f, 1.f);
-            // a1: node position in double-float, k_0 = q/2, k_0^2
-            float qh, ql;
+            const float4 qd = sh_qd[si_q];
+            // a1: node position k_0 = q/2 in double-float (Q and dQ are staged
+            // halved, exactly), k_0^2
+            float k0h, k0l;
             {
                 const float th = __fmul_rn(qd.y, g_hi);
                 float tl = fmaf(qd.y, g_hi, -th);
@@ -705,11 +722,10 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 float s, e;
                 two_sum(qd.x, th, s, e);
                 e = __fadd_rn(e, tl);
-                fast_two_sum(s, e, qh, ql);
+                fast_two_sum(s, e, k0h, k0l);
             }
-            const bool qok = qh > 0.f;
+            const bool qok = k0h > 0.f;
             if (act && !qok) atomicOr(ka.status, NR_FLAG_BAD_Q);
-            const float k0h = 0.5f * qh, k0l = 0.5f * ql;
             const float p_hi = __fmul_rn(k0h, k0h);
             float p_lo = fmaf(k0h, k0h, -p_hi);
             p_lo = fmaf(2.f * k0h, k0l, p_lo);
@@ -739,11 +755,11 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 } else {
                     kj = medium_kz<true>(p_hi, p_lo, sm.c[j], sm.a[j]);
                 }
-                float2 Gj;
+                float2 Gj, kkj;
                 // k_0 is real: the unrolled sweeps use the real-k_a form there
                 const float2 rj = (T::UNROLL && j == 0)
-                                      ? fresnel_nc<true>(kc(kj), kc(kbelow), sm.N[j], sm.s[j], sm.sl[j], Gj)
-                                      : fresnel_nc<false>(kc(kj), kc(kbelow), sm.N[j], sm.s[j], sm.sl[j], Gj);
+                                      ? fresnel_nc<true>(kc(kj), kc(kbelow), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj)
+                                      : fresnel_nc<false>(kc(kj), kc(kbelow), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj);
                 float2 Xj;
                 if (j == n) {
                     Xj = rj;
@@ -774,7 +790,9 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             // a8-a10: smearing sum, model, likelihood, adjoint seed.  Every
             // lane of a Q point forms the same sum from shared memory, so the
             // seed needs no second barrier.
-            if (lane_on) sh_wR[buf][qslot * KP + kn] = act ? wk * R : 0.f;
+            // (a lane past the item's last Q point adds a finite value to
+            // a slot whose sum is never used)
+            if (lane_on) sh_wR[buf][qslot * KP + kn] = wk * R;
             __syncthreads();
             float Rb = 0.f;
             // smearing sums of the Q slots this warp touches: sgl lanes per
@@ -796,7 +814,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 const float m = fmaf(scale, S, bkg);
                 const float res = (m - qd.z) * qd.w; // (m - R) / err
                 if (act && kn == 0) sh_rs[si_q] = make_float2(res, S);
-                if constexpr (GRAD) Rb = act ? wks * -(res * qd.w) : 0.f; // w_k scale dl/dm
+                if constexpr (GRAD) Rb = wks * -(res * qd.w); // w_k scale dl/dm (0 on idle lanes)
             }
             if constexpr (GRAD) {
                 // a7: adjoint sweep from the fronting down to the backing
@@ -811,7 +829,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     const float2 Xb_in = Xb;
                     float2 Zj = make_float2(0.f, 0.f);
                     Kz kj1;
-                    float2 rj, Gj;
+                    float2 rj, Gj, kkj;
                     if constexpr (T::STORE) {
                         kj1 = kst[j + 1];
                         rj = rst[j];
@@ -820,8 +838,8 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         kj1 = (j == n) ? medium_kz<false>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1])
                                        : medium_kz<true>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1]);
                         rj = (T::UNROLL && j == 0)
-                                 ? fresnel_nc<true>(kc(kj), kc(kj1), sm.N[j], sm.s[j], sm.sl[j], Gj)
-                                 : fresnel_nc<false>(kc(kj), kc(kj1), sm.N[j], sm.s[j], sm.sl[j], Gj);
+                                 ? fresnel_nc<true>(kc(kj), kc(kj1), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj)
+                                 : fresnel_nc<false>(kc(kj), kc(kj1), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj);
                     }
                     float2 kbar1 = make_float2(0.f, 0.f);
                     float2 rb;
@@ -841,12 +859,11 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                             Dj = make_float2(dx * inv, -dy * inv);
                         }
                         Zj = Y;
-                        const float2 one = make_float2(1.f, 0.f);
                         // dX/dr = (1 - Y^2) D^2, dX/dY = (1 - r^2) D^2: both
                         // adjoints share V = conj(D^2) Xbar
-                        const float2 V = cmulc(csqr(Dj), Xb);
-                        rb = cmulc(csub(one, csqr(Y)), V);
-                        const float2 Yb = cmulc(csub(one, csqr(rj)), V);
+                        const float2 V = cmulc(Dj, cmulc(Dj, Xb));
+                        rb = cmulc(one_minus_sq(Y), V);
+                        const float2 Yb = cmulc(one_minus_sq(rj), V);
                         Xb = cmulc(Ej1, Yb);
                         // Y = X_{j+1} E_{j+1}: dY/dd = 2 i k Y and dY/dk = 2 i d Y.
                         // With U = conj(Y) Ybar the d_{j+1} sum takes
@@ -859,25 +876,24 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         rb = Xb;
                     }
                     // dr/dk_j = k_{j+1} P and dr/dk_{j+1} = k_j M with
-                    // P = 2G + s r, M = s r - 2G
+                    // P = 2G + s r, M = s r - 2G.  With rr = conj(rbar) r
+                    // (also the roughness term) and g = conj(G) rbar:
+                    // conj(M) rbar = s conj(rr) - 2g, conj(P) rbar = s conj(rr) + 2g
                     const float sj = sm.s[j];
-                    const float2 A = make_float2(sj * rj.x, sj * rj.y);
-                    const float2 P = make_float2(fmaf(2.f, Gj.x, A.x), fmaf(2.f, Gj.y, A.y));
-                    const float2 M = make_float2(fmaf(-2.f, Gj.x, A.x), fmaf(-2.f, Gj.y, A.y));
-                    const float2 H = cmulc(M, rb);               // kbar_{j+1} += conj(k_j) H
                     const float2 rr = cmulc(rb, rj);             // accS += Re(rr k_j k_{j+1})
+                    const float2 gg = cmulc(Gj, rb);
+                    const float2 sr = make_float2(sj * rr.x, -sj * rr.y);
+                    const float2 H = make_float2(fmaf(-2.f, gg.x, sr.x), fmaf(-2.f, gg.y, sr.y)); // conj(M) rbar
                     const bool k_real = T::UNROLL && j == 0;     // k_0 is real
-                    float2 kk;
-                    if (k_real) {
-                        kbar1 = make_float2(fmaf(kj.re, H.x, kbar1.x), fmaf(kj.re, H.y, kbar1.y));
-                        kk = make_float2(kj.re * kj1.re, kj.re * kj1.im);
-                    } else {
-                        kbar1 = cfmac(kc(kj), H, kbar1);
-                        kk = cmul(kc(kj), kc(kj1));
-                    }
-                    acc_fma2(oS + j, rr.x, kk.x, -rr.y, kk.y);
+                    if (k_real) kbar1 = make_float2(fmaf(kj.re, H.x, kbar1.x), fmaf(kj.re, H.y, kbar1.y));
+                    else kbar1 = cfmac(kc(kj), H, kbar1);
+                    // k_j k_{j+1} (the recomputing sweeps have it from fresnel_nc)
+                    if constexpr (T::STORE)
+                        kkj = k_real ? make_float2(kj.re * kj1.re, kj.re * kj1.im) : cmul(kc(kj), kc(kj1));
+                    acc_fma2(oS + j, rr.x, kkj.x, -rr.y, kkj.y);
                     if (j >= 1) {
-                        kbar = cfmac(kc(kj1), cmulc(P, rb), kbar);
+                        const float2 H2 = make_float2(fmaf(2.f, gg.x, sr.x), fmaf(2.f, gg.y, sr.y)); // conj(P) rbar
+                        kbar = cfmac(kc(kj1), H2, kbar);
                         // k_j complete: accumulate conj(kbar) / k_j, or queue
                         // the interior-edge evaluation for this lane
                         const float m2 = fmaf(kj.re, kj.re, kj.im * kj.im);
