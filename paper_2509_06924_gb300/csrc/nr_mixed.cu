@@ -72,6 +72,14 @@ constexpr float kEdgeFrac = NR_EDGE_FRAC;
 #ifndef NR_BLOCK_GRAD1
 #define NR_BLOCK_GRAD1 128
 #endif
+// CTAs per SM of the 2- and 4-layer gradient buckets
+#ifndef NR_MINB_SMALL
+#define NR_MINB_SMALL 3
+#endif
+// gradient buckets of at least this many layers run 128-thread CTAs
+#ifndef NR_DEEP_BLOCK128
+#define NR_DEEP_BLOCK128 16
+#endif
 // 1: Nevot-Croce phase and |u + i a| are computed without data-dependent
 // branches (a few more XU operations, straight-line code)
 #ifndef NR_BRANCHFREE
@@ -395,7 +403,8 @@ struct Traits {
     static constexpr int NM = NMAX > 0 ? NMAX : NR_MAX_LAYERS; // smem capacity
     // deep gradient buckets run 128-thread CTAs so that their per-thread
     // state in shared memory still leaves room for several CTAs per SM
-    static constexpr int BLOCK = !kGradMode ? (NMAX == 1 ? NR_BLOCK_FWD1 : 256) : NMAX == 1 ? NR_BLOCK_GRAD1 : NMAX >= 16 ? 128 : 256;
+    static constexpr int BLOCK = !kGradMode ? (NMAX == 1 ? NR_BLOCK_FWD1 : 256)
+                                 : NMAX == 1 ? NR_BLOCK_GRAD1 : NMAX >= NR_DEEP_BLOCK128 ? 128 : 256;
     static constexpr bool STORE = kGradMode && NMAX <= 2;     // keep all intermediates
     static constexpr bool UNROLL = NMAX >= 1 && NMAX <= 4;    // register arrays, unrolled sweeps
     static constexpr bool SMEM_ACC = kGradMode && !UNROLL;    // partials in shared memory
@@ -410,7 +419,7 @@ struct Traits {
 #define NR_DEEP_REGS 96
 #endif
     // register caps: rolled deep kernels are held to NR_DEEP_REGS per thread
-    static constexpr int MINB = !kGradMode ? (NMAX == 1 ? NR_MINB_FWD1 : NR_MINB_FWD) : NMAX == 1 ? NR_MINB_GRAD1 : NMAX <= 4 ? 3
+    static constexpr int MINB = !kGradMode ? (NMAX == 1 ? NR_MINB_FWD1 : NR_MINB_FWD) : NMAX == 1 ? NR_MINB_GRAD1 : NMAX <= 4 ? NR_MINB_SMALL
                                 : 65536 / (BLOCK * NR_DEEP_REGS);
     // Q points staged in shared memory per super-tile (several tiles)
     static constexpr int CAPQ = SMEM_ACC ? 96 : 256;
@@ -1084,7 +1093,8 @@ template <int MODE, int NMAX, int KC>
 cudaError_t set_smem_attr()
 {
     using T = Traits<MODE, NMAX>;
-    if (T::DYN > 48 * 1024)
+    // the default cap on dynamic shared memory is 48 KB less the static use
+    if (T::DYN > 0)
         return cudaFuncSetAttribute(nr_mixed_kernel<MODE, NMAX, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)T::DYN);
     return cudaSuccess;
