@@ -46,20 +46,27 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 
 
-def flops_per_eval(n: int, absorbing: bool, K: int) -> float:
+def flops_per_eval(n: int, K: int) -> float:
     """Algorithmic FP32 flops of one fwd+grad evaluation of an n-layer stack
-    (FMA = 2), counted from the kernel source; the table and its derivation
-    are in the design notes.  Transcendental (XU) ops are not counted."""
-    med = 28 if absorbing else 24          # k_j: double-float k0^2 - c_j, rsqrt, Newton step
-    fres = 33                              # r_j with Nevot-Croce factor
-    phase = 22                             # E_j: double-float phase, mod-2pi reduction
-    mob = 26                               # Parratt / Moebius step
-    fwd = 26 + (n + 1) * (med + fres) + n * (phase + mob)
-    adj = 3 + 83 * n + 74 * (n + 1)
-    if n > 2:                              # deeper stacks recompute k, r, E in the adjoint
-        adj += (n + 1) * (med + fres) + n * (phase + 12)
-    per_q = (K + 15.0) / K + 2.0           # smearing sum, likelihood, seeds
-    return float(fwd + adj + per_q)
+    (FMA = 2), counted term by term from the gradient kernel's source.  Not
+    counted: transcendental (XU) operations, compares and selects, and the
+    redundant copies of the smearing sum that every lane of a Q point forms."""
+    unrolled, store = n <= 4, n <= 2
+    fres0 = 29 if unrolled else 34         # r_0: k_0 is real in the unrolled sweeps
+    # node q (double-float) 15, k_0^2 6, backing k 10, |X|^2 3; per layer:
+    # k_j with Newton step 25, r_j 34, E_j 18, Y_j 6, Moebius step 20
+    fwd = 15 + 6 + 10 + fres0 + 3 + n * (25 + 34 + 18 + 6 + 20)
+    seed = 11                              # smearing, model, residual, adjoint seed
+    # adjoint: Moebius/phase terms 54 per layer, Fresnel/roughness terms 22 per
+    # interface, k_j adjoint 8 (4 for the real k_0) and 1/k_j terms 25 per
+    # layer, backing medium 13
+    adj = 54 * n + 22 * (n + 1) + 8 * n + (4 if unrolled else 8) + 25 * n + 13
+    if store:
+        adj += 2 + 6 * n                   # k_j k_{j+1}, re-formed from the kept k_j
+    else:                                  # k, r, E, D recomputed top-down
+        adj += (25 * n + 10) + (fres0 + 34 * n) + 36 * n
+    per_q = 15.0 / K                       # likelihood terms, once per Q point
+    return float(fwd + seed + adj + per_q)
 
 
 def peak_fp32_tflops(mhz: float = SM_MAX_MHZ_NOMINAL) -> float:
@@ -339,9 +346,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    absorbing = bool(np.any(wl.params[np.concatenate([np.arange(po + 2 * n + 2, po + 3 * n + 3)
-                                                      for po, n in zip(wl.par_off[:-1], wl.n_layers)])] > 0))
-    flops = sum(flops_per_eval(int(n), absorbing, wl.n_quad) * (wl.out_off[s + 1] - wl.out_off[s]) * wl.n_quad
+    flops = sum(flops_per_eval(int(n), wl.n_quad) * (wl.out_off[s + 1] - wl.out_off[s]) * wl.n_quad
                 for s, n in enumerate(wl.n_layers))
     kernel_ms = ms  # the step is one launch of the gradient kernel per layer bucket
     achieved = flops / (kernel_ms * 1e-3) / 1e12
