@@ -51,8 +51,8 @@ def flops_per_eval(n: int, K: int) -> float:
     (FMA = 2), counted term by term from the gradient kernel's source.  Not
     counted: transcendental (XU) operations, compares and selects, and the
     redundant copies of the smearing sum that every lane of a Q point forms."""
-    unrolled, store = n <= 4, n <= 2
-    fres0 = 29 if unrolled else 34         # r_0: k_0 is real in the unrolled sweeps
+    store = n <= 2
+    fres0 = 29                             # r_0: k_0 is real
     # node q (double-float) 15, k_0^2 6, backing k 10, |X|^2 3; per layer:
     # k_j with Newton step 25, r_j 34, E_j 18, Y_j 6, Moebius step 20
     fwd = 15 + 6 + 10 + fres0 + 3 + n * (25 + 34 + 18 + 6 + 20)
@@ -60,7 +60,7 @@ def flops_per_eval(n: int, K: int) -> float:
     # adjoint: Moebius/phase terms 54 per layer, Fresnel/roughness terms 22 per
     # interface, k_j adjoint 8 (4 for the real k_0) and 1/k_j terms 25 per
     # layer, backing medium 13
-    adj = 54 * n + 22 * (n + 1) + 8 * n + (4 if unrolled else 8) + 25 * n + 13
+    adj = 54 * n + 22 * (n + 1) + 8 * n + 4 + 25 * n + 13
     if store:
         adj += 2 + 6 * n                   # k_j k_{j+1}, re-formed from the kept k_j
     else:                                  # k, r, E, D recomputed top-down

@@ -31,6 +31,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "nr_internal.h"
 
@@ -85,10 +86,27 @@ constexpr float kEdgeFrac = NR_EDGE_FRAC;
 #ifndef NR_BRANCHFREE
 #define NR_BRANCHFREE 1
 #endif
+// unroll factor of the rolled (deep) forward and adjoint sweeps
+#ifndef NR_DEEP_UNROLL
+#define NR_DEEP_UNROLL 2
+#endif
+constexpr int kDeepUnroll = NR_DEEP_UNROLL;
 // 1: the 1-layer kernels treat n as the compile-time constant 1
 #ifndef NR_EXACT1
 #define NR_EXACT1 1
 #endif
+
+// Position of a sweep step, known at compile time or tested at run time: the
+// rolled sweeps peel their first and last steps so that the steps between
+// them carry no branches on j.
+enum : int { kNo = 0, kYes = 1, kRt = 2 };
+template <int V>
+using Pos = std::integral_constant<int, V>;
+template <class P>
+__device__ __forceinline__ bool pos_flag(P, bool rt)
+{
+    return P::value == kRt ? rt : P::value == kYes;
+}
 
 // ------------------------------------------------------------ primitives --
 __device__ __forceinline__ float rcp_approx(float x)
@@ -757,20 +775,21 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             };
             Kz kbelow = medium_kz<false>(p_hi, p_lo, sm.c[n + 1], sm.a[n + 1]);
             float2 Xbelow = make_float2(0.f, 0.f);
-            auto fwd_step = [&](int j) __attribute__((always_inline)) {
+            // TOP: j == 0 (fronting), BOT: j == n (last interface)
+            auto fwd_step = [&](int j, auto TOP, auto BOT) __attribute__((always_inline)) {
+                const bool top = pos_flag(TOP, j == 0), bot = pos_flag(BOT, j == n);
                 Kz kj;
-                if (j == 0) {
+                if (top) {
                     kj.re = k0h; kj.im = 0.f; kj.lo = k0l;
                 } else {
                     kj = medium_kz<true>(p_hi, p_lo, sm.c[j], sm.a[j]);
                 }
                 float2 Gj, kkj;
-                // k_0 is real: the unrolled sweeps use the real-k_a form there
-                const float2 rj = (T::UNROLL && j == 0)
-                                      ? fresnel_nc<true>(kc(kj), kc(kbelow), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj)
+                // k_0 is real: the real-k_a form there
+                const float2 rj = top ? fresnel_nc<true>(kc(kj), kc(kbelow), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj)
                                       : fresnel_nc<false>(kc(kj), kc(kbelow), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj);
                 float2 Xj;
-                if (j == n) {
+                if (bot) {
                     Xj = rj;
                     if constexpr (T::STORE) kst[j + 1] = kbelow;
                 } else {
@@ -788,10 +807,12 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             if constexpr (T::UNROLL) {
 #pragma unroll
                 for (int j = NM; j >= 0; --j)
-                    if (j <= n) fwd_step(j);
+                    if (j <= n) fwd_step(j, Pos<kRt>{}, Pos<kRt>{});
             } else {
-#pragma unroll 1
-                for (int j = n; j >= 0; --j) fwd_step(j);
+                fwd_step(n, Pos<kRt>{}, Pos<kYes>{});
+#pragma unroll kDeepUnroll
+                for (int j = n - 1; j >= 1; --j) fwd_step(j, Pos<kNo>{}, Pos<kNo>{});
+                if (n >= 1) fwd_step(0, Pos<kYes>{}, Pos<kNo>{});
             }
             float R = Xbelow.x * Xbelow.x + Xbelow.y * Xbelow.y;
             if (!qok) R = __int_as_float(0x7fffffff);
@@ -834,7 +855,8 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 Kz kjm1 = kj;                          // k_{j-1}
                 float2 Xb_up = make_float2(0.f, 0.f);  // adjoint of X_{j-1}
                 const float edge_u = kEdgeFrac * k0h * k0h;
-                auto adj_step = [&](int j) __attribute__((always_inline)) {
+                auto adj_step = [&](int j, auto TOP, auto BOT) __attribute__((always_inline)) {
+                    const bool top = pos_flag(TOP, j == 0), bot = pos_flag(BOT, j == n);
                     const float2 Xb_in = Xb;
                     float2 Zj = make_float2(0.f, 0.f);
                     Kz kj1;
@@ -844,15 +866,14 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         rj = rst[j];
                         Gj = Gst[j];
                     } else {
-                        kj1 = (j == n) ? medium_kz<false>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1])
-                                       : medium_kz<true>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1]);
-                        rj = (T::UNROLL && j == 0)
-                                 ? fresnel_nc<true>(kc(kj), kc(kj1), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj)
+                        kj1 = bot ? medium_kz<false>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1])
+                                  : medium_kz<true>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1]);
+                        rj = top ? fresnel_nc<true>(kc(kj), kc(kj1), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj)
                                  : fresnel_nc<false>(kc(kj), kc(kj1), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj);
                     }
                     float2 kbar1 = make_float2(0.f, 0.f);
                     float2 rb;
-                    if (j < n) {
+                    if (!bot) {
                         const float2 X1 = Xget(j + 1);
                         float2 Ej1, Dj, Y;
                         if constexpr (T::STORE) {
@@ -893,14 +914,14 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     const float2 gg = cmulc(Gj, rb);
                     const float2 sr = make_float2(sj * rr.x, -sj * rr.y);
                     const float2 H = make_float2(fmaf(-2.f, gg.x, sr.x), fmaf(-2.f, gg.y, sr.y)); // conj(M) rbar
-                    const bool k_real = T::UNROLL && j == 0;     // k_0 is real
+                    const bool k_real = top;                     // k_0 is real
                     if (k_real) kbar1 = make_float2(fmaf(kj.re, H.x, kbar1.x), fmaf(kj.re, H.y, kbar1.y));
                     else kbar1 = cfmac(kc(kj), H, kbar1);
                     // k_j k_{j+1} (the recomputing sweeps have it from fresnel_nc)
                     if constexpr (T::STORE)
                         kkj = k_real ? make_float2(kj.re * kj1.re, kj.re * kj1.im) : cmul(kc(kj), kc(kj1));
                     acc_fma2(oS + j, rr.x, kkj.x, -rr.y, kkj.y);
-                    if (j >= 1) {
+                    if (!top) {
                         const float2 H2 = make_float2(fmaf(2.f, gg.x, sr.x), fmaf(2.f, gg.y, sr.y)); // conj(P) rbar
                         kbar = cfmac(kc(kj1), H2, kbar);
                         // k_j complete: accumulate conj(kbar) / k_j, or queue
@@ -937,7 +958,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     kbar = kbar1;
                     kjm1 = kj;
                     kj = kj1;
-                    if (j == n) { // backing medium n+1: its k is complete as well
+                    if (bot) { // backing medium n+1: its k is complete as well
                         const float2 kk = cmul(kbar, kc(kj));
                         const float m2 = fmaf(kj.re, kj.re, kj.im * kj.im);
                         const float inv = m2 > 0.f ? rcp_approx(m2) : 0.f;
@@ -948,15 +969,17 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 if constexpr (T::UNROLL) {
 #pragma unroll
                     for (int j = 0; j <= NM; ++j)
-                        if (j <= n) adj_step(j);
+                        if (j <= n) adj_step(j, Pos<kRt>{}, Pos<kRt>{});
                     // drain full batches of the interior-edge queue
                     while (eq_cnt >= 32) {
                         __syncwarp();
                         eq_drain(32);
                     }
                 } else {
-#pragma unroll 1
-                    for (int j = 0; j <= n; ++j) adj_step(j);
+                    if (n >= 1) adj_step(0, Pos<kYes>{}, Pos<kNo>{});
+#pragma unroll kDeepUnroll
+                    for (int j = 1; j <= n - 1; ++j) adj_step(j, Pos<kNo>{}, Pos<kNo>{});
+                    adj_step(n, Pos<kRt>{}, Pos<kYes>{});
                 }
             }
         }
