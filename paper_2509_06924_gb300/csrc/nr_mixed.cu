@@ -231,8 +231,9 @@ __device__ __forceinline__ Kz kz_sqrt(float uh, float ul, float2 aa)
 // p_hi - c_hi is exact near the critical edge (Sterbenz) and the low words
 // keep the rest to FP32 accuracy.
 template <bool REFINE>
-__device__ __forceinline__ Kz medium_kz(float p_hi, float p_lo, float2 c, float2 a)
+__device__ __forceinline__ Kz medium_kz(float p_hi, float p_lo, float4 m)
 {
+    const float2 c = make_float2(m.x, m.y), a = make_float2(m.z, m.w);
     if constexpr (REFINE) {
         float uh, ul;
         two_sum(p_hi, -c.x, uh, ul);
@@ -248,9 +249,11 @@ __device__ __forceinline__ Kz medium_kz(float p_hi, float p_lo, float2 c, float2
 // E = exp(2 i k d).  The real phase 2 Re(k) d is formed in double-float and
 // reduced modulo 2 pi (Cody-Waite, two-word 2 pi; the multiple of 2 pi is
 // rounded with the 1.5 * 2^23 addition) before the FP32 sincos.
-// d2 = 2 d as (hi, lo); ea = -2 d log2(e), so |E| = 2^(Im(k) ea).
-__device__ __forceinline__ float2 layer_phase(const Kz &k, float2 d2, float ea)
+// L = (2 d as (hi, lo), ea = -2 d log2(e), -): |E| = 2^(Im(k) ea).
+__device__ __forceinline__ float2 layer_phase(const Kz &k, float4 L)
 {
+    const float2 d2 = make_float2(L.x, L.y);
+    const float ea = L.z;
     const float t = k.re, tl = k.lo;
     const float ph = __fmul_rn(t, d2.x);
     float pl = fmaf(t, d2.x, -ph);
@@ -267,12 +270,14 @@ __device__ __forceinline__ float2 layer_phase(const Kz &k, float2 d2, float ea)
 }
 
 // r_j with Nevot-Croce roughness; also returns G = exp(s k_a k_b) / S^2 with
-// S = k_a + k_b (the adjoint needs it) and kk = k_a k_b: r = N G.  sl = s log2(e).  REAL_A:
+// S = k_a + k_b (the adjoint needs it) and kk = k_a k_b: r = N G.  I = (N, s,
+// sl = s log2(e)).  REAL_A:
 // k_a is real (the fronting medium), its imaginary part is not read.
 template <bool REAL_A>
-__device__ __forceinline__ float2 fresnel_nc(float2 ka, float2 kb, float2 N, float s, float sl, float2 &G,
-                                             float2 &kk)
+__device__ __forceinline__ float2 fresnel_nc(float2 ka, float2 kb, float4 I, float2 &G, float2 &kk)
 {
+    const float2 N = make_float2(I.x, I.y);
+    const float s = I.z, sl = I.w;
     const float Sx = ka.x + kb.x, Sy = REAL_A ? kb.y : ka.y + kb.y;
     const float n2 = fmaf(Sx, Sx, Sy * Sy);
     const float inv = n2 > 0.f ? rcp_approx(n2) : 0.f;
@@ -395,19 +400,40 @@ __device__ __forceinline__ float2 edge_ubar(float2 a, float2 k, float2 b, float 
     return cmulc(dXdu, Xbar_up);
 }
 
+// k_0^2 = (p_hi + p_lo) from k_0 = (k0h + k0l), double-float
+__device__ __forceinline__ void k0_square(float k0h, float k0l, float &p_hi, float &p_lo)
+{
+    p_hi = __fmul_rn(k0h, k0h);
+    p_lo = fmaf(k0h, k0h, -p_hi);
+    p_lo = fmaf(2.f * k0h, k0l, p_lo);
+}
+
+// One queued interior-edge evaluation: the entry keeps the node k_0 (hi, lo),
+// Z and Xbar_{j-1}; k_{j-1}, k_j and k_{j+1} are formed again from the node
+// exactly as the sweeps form them.
+__device__ __forceinline__ float2 edge_entry_ubar(float2 node, float2 Z, float2 Xbu, int j, int n,
+                                                  const float4 *med, const float4 *lay)
+{
+    float p_hi, p_lo;
+    k0_square(node.x, node.y, p_hi, p_lo);
+    const Kz ka = j == 1 ? Kz{node.x, 0.f, node.y} : medium_kz<true>(p_hi, p_lo, med[j - 1]);
+    const Kz kj = medium_kz<true>(p_hi, p_lo, med[j]);
+    const Kz kb = j == n ? medium_kz<false>(p_hi, p_lo, med[j + 1]) : medium_kz<true>(p_hi, p_lo, med[j + 1]);
+    return edge_ubar(kc(ka), kc(kj), kc(kb), lay[j - 1].w, lay[j].w, 0.5f * lay[j].x, Z, j == n, Xbu);
+}
+
 // Drains `cnt` queued interior-edge entries of one warp (one per lane) into
 // per-thread partials kept in shared memory (acc points at this thread's
 // slot of medium 1's Re-accumulator; stride between accumulators `stride`,
-// Re -> Im distance `im_off`; d2: twice the layer thicknesses).  Kept out of
-// line so that the rolled sweep it is called from keeps its register budget.
+// Re -> Im distance `im_off`; med, lay: the staged stack entries).  Kept out
+// of line so that the rolled sweep it is called from keeps its register budget.
 template <int EQ>
-__device__ __noinline__ void eq_drain_smem(float2 (*q)[EQ], const int *qj, const float *sg, const float2 *d2, int n,
-                                           int lane, int cnt, float *acc, int stride, int im_off)
+__device__ __noinline__ void eq_drain_smem(float2 (*q)[EQ], const int *qj, const float4 *med, const float4 *lay,
+                                           int n, int lane, int cnt, float *acc, int stride, int im_off)
 {
     if (lane < cnt) {
         const int j = qj[lane];
-        const float2 ub = edge_ubar(q[0][lane], q[1][lane], q[2][lane], sg[j - 1], sg[j], 0.5f * d2[j].x, q[3][lane],
-                                    j == n, q[4][lane]);
+        const float2 ub = edge_entry_ubar(q[0][lane], q[1][lane], q[2][lane], j, n, med, lay);
         // conj(kbar)/k_j = 2 conj(ubar)
         acc[(j - 1) * stride] += 2.f * ub.x;
         acc[(j - 1) * stride + im_off] += -2.f * ub.y;
@@ -446,17 +472,14 @@ struct Traits {
                                   (X_SMEM ? (size_t)(NM + 1) * BLOCK * 8 : 0);
 };
 
-// Per-stack parameters staged in shared memory.
+// Per-stack parameters staged in shared memory, one 16-byte entry per
+// medium, interface and layer (a sweep step reads each with one load).
 template <int NM>
 struct StackSmem {
-    float2 c[NM + 2];  // 4 pi (rho_j - rho_0) as (hi, lo), j = 1..n+1
-    float2 a[NM + 2];  // 4 pi iota_j and its square, j = 1..n+1
-    float2 N[NM + 1];  // 4 pi (rho_{j+1} - rho_j) + 4 pi i (iota_j - iota_{j+1})
-    float s[NM + 1];   // -2 sigma_j^2
-    float sl[NM + 1];  // -2 sigma_j^2 log2(e)
-    float sg[NM + 1];  // sigma_j
-    float2 d2[NM + 2]; // twice the thickness (hi, lo), j = 1..n
-    float ea[NM + 2];  // -2 d_j log2(e)
+    float4 med[NM + 2]; // medium j = 1..n+1: 4 pi (rho_j - rho_0) as (hi, lo), 4 pi iota_j, its square
+    float4 itf[NM + 1]; // interface j = 0..n: 4 pi (rho_{j+1} - rho_j) + 4 pi i (iota_j - iota_{j+1}),
+                        // s_j = -2 sigma_j^2, s_j log2(e)
+    float4 lay[NM + 2]; // layer j = 1..n: 2 d_j as (hi, lo), -2 d_j log2(e); sigma_j (j = 0..n)
     float scale, bkg;
 };
 
@@ -474,16 +497,19 @@ __device__ void stage_stack(StackSmem<NM> &sm, const double *p, int n, int tid, 
         const int j = tid;
         const double rho0 = p[n];
         bool bad = false;
+        float4 lay = make_float4(0.f, 0.f, 0.f, 0.f);
         if (j >= 1) {
             const double rj = p[n + j];
             const double ij = p[2 * n + 2 + j - 1];
-            sm.c[j] = split_double(kFourPiD * (rj - rho0));
-            sm.a[j] = make_float2((float)(kFourPiD * ij), (float)(kFourPiD * kFourPiD * ij * ij));
+            const float2 c = split_double(kFourPiD * (rj - rho0));
+            sm.med[j] = make_float4(c.x, c.y, (float)(kFourPiD * ij), (float)(kFourPiD * kFourPiD * ij * ij));
             bad |= !isfinite(rj) || !isfinite(ij);
             if (j <= n) {
                 const double dj = p[j - 1];
-                sm.d2[j] = split_double(2.0 * dj);
-                sm.ea[j] = (float)(-2.0 * kLog2ED * dj);
+                const float2 d2 = split_double(2.0 * dj);
+                lay.x = d2.x;
+                lay.y = d2.y;
+                lay.z = (float)(-2.0 * kLog2ED * dj);
                 bad |= !isfinite(dj);
             }
         } else {
@@ -493,13 +519,13 @@ __device__ void stage_stack(StackSmem<NM> &sm, const double *p, int n, int tid, 
             const double iot_j = j >= 1 ? p[2 * n + 2 + j - 1] : 0.0;
             const double iot_j1 = p[2 * n + 2 + j];
             const double sig = p[3 * n + 3 + j];
-            sm.N[j] = make_float2((float)(kFourPiD * (p[n + j + 1] - p[n + j])),
-                                  (float)(kFourPiD * (iot_j - iot_j1)));
-            sm.s[j] = (float)(-2.0 * sig * sig);
-            sm.sl[j] = (float)(-2.0 * kLog2ED * sig * sig);
-            sm.sg[j] = (float)sig;
+            sm.itf[j] = make_float4((float)(kFourPiD * (p[n + j + 1] - p[n + j])),
+                                    (float)(kFourPiD * (iot_j - iot_j1)), (float)(-2.0 * sig * sig),
+                                    (float)(-2.0 * kLog2ED * sig * sig));
+            lay.w = (float)sig;
             bad |= !isfinite(sig);
         }
+        sm.lay[j] = lay;
         if (j == 0) {
             sm.scale = (float)p[4 * n + 4];
             sm.bkg = (float)p[4 * n + 5];
@@ -564,8 +590,11 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     __shared__ double sh_raw[T::NRAW];
     __shared__ int sh_item;
     __shared__ int sh_last;
-    // interior-edge queue per warp: a, k, b, Z, Xbar (complex) and the medium
-    __shared__ float2 sh_eq[GRAD ? T::WARPS : 1][5][EQ];
+    // interior-edge queue per warp: k_{j-1}, k_j, k_{j+1}, Z, Xbar_{j-1} and
+    // the medium j; the rolled sweeps keep the node k_0 in place of the three
+    // wavevectors (smaller entries, more CTAs per SM)
+    constexpr int EQF = T::SMEM_ACC ? 3 : 5;
+    __shared__ float2 sh_eq[GRAD ? T::WARPS : 1][EQF][EQ];
     __shared__ int sh_eqj[GRAD ? T::WARPS : 1][EQ];
     extern __shared__ __align__(16) float sh_dyn[]; // [NACC][BLOCK] partials, then [NM+1][BLOCK] X_j
     float *sh_acc = sh_dyn;
@@ -651,13 +680,13 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
         // drain `cnt` <= 32 queued entries, one per lane, then shift the rest down
         auto eq_drain = [&](int cnt) {
             if constexpr (T::SMEM_ACC) {
-                eq_drain_smem<EQ>(sh_eq[warp], sh_eqj[warp], sm.sg, sm.d2, n, lane, cnt, sh_acc + oUr * BLOCK + tid,
+                eq_drain_smem<EQ>(sh_eq[warp], sh_eqj[warp], sm.med, sm.lay, n, lane, cnt, sh_acc + oUr * BLOCK + tid,
                                   BLOCK, (oUi - oUr) * BLOCK);
             } else if (lane < cnt) {
                 const int j = sh_eqj[warp][lane];
                 const float2 ub = edge_ubar(sh_eq[warp][0][lane], sh_eq[warp][1][lane], sh_eq[warp][2][lane],
-                                            sm.sg[j - 1], sm.sg[j], 0.5f * sm.d2[j].x, sh_eq[warp][3][lane], j == n,
-                                            sh_eq[warp][4][lane]);
+                                            sm.lay[j - 1].w, sm.lay[j].w, 0.5f * sm.lay[j].x, sh_eq[warp][3][lane],
+                                            j == n, sh_eq[warp][4][lane]);
                 // conj(kbar)/k_j = 2 conj(ubar)
                 acc_u(j, make_float2(2.f * ub.x, -2.f * ub.y));
             }
@@ -666,7 +695,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             for (int e = lane; e < rest; e += 32) {
                 const int src = cnt + e;
 #pragma unroll
-                for (int f = 0; f < 5; ++f) sh_eq[warp][f][e] = sh_eq[warp][f][src];
+                for (int f = 0; f < EQF; ++f) sh_eq[warp][f][e] = sh_eq[warp][f][src];
                 sh_eqj[warp][e] = sh_eqj[warp][src];
             }
             __syncwarp();
@@ -753,9 +782,8 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
             }
             const bool qok = k0h > 0.f;
             if (act && !qok) atomicOr(ka.status, NR_FLAG_BAD_Q);
-            const float p_hi = __fmul_rn(k0h, k0h);
-            float p_lo = fmaf(k0h, k0h, -p_hi);
-            p_lo = fmaf(2.f * k0h, k0l, p_lo);
+            float p_hi, p_lo;
+            k0_square(k0h, k0l, p_hi, p_lo);
 
             // a3-a6 forward, from the backing upwards
             Kz kst[T::STORE ? NM + 2 : 1];
@@ -773,7 +801,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 else if constexpr (GRAD) return Xr[j];
                 else return make_float2(0.f, 0.f);
             };
-            Kz kbelow = medium_kz<false>(p_hi, p_lo, sm.c[n + 1], sm.a[n + 1]);
+            Kz kbelow = medium_kz<false>(p_hi, p_lo, sm.med[n + 1]);
             float2 Xbelow = make_float2(0.f, 0.f);
             // TOP: j == 0 (fronting), BOT: j == n (last interface)
             auto fwd_step = [&](int j, auto TOP, auto BOT) __attribute__((always_inline)) {
@@ -782,18 +810,19 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 if (top) {
                     kj.re = k0h; kj.im = 0.f; kj.lo = k0l;
                 } else {
-                    kj = medium_kz<true>(p_hi, p_lo, sm.c[j], sm.a[j]);
+                    kj = medium_kz<true>(p_hi, p_lo, sm.med[j]);
                 }
                 float2 Gj, kkj;
                 // k_0 is real: the real-k_a form there
-                const float2 rj = top ? fresnel_nc<true>(kc(kj), kc(kbelow), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj)
-                                      : fresnel_nc<false>(kc(kj), kc(kbelow), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj);
+                const float4 Ij = sm.itf[j];
+                const float2 rj = top ? fresnel_nc<true>(kc(kj), kc(kbelow), Ij, Gj, kkj)
+                                      : fresnel_nc<false>(kc(kj), kc(kbelow), Ij, Gj, kkj);
                 float2 Xj;
                 if (bot) {
                     Xj = rj;
                     if constexpr (T::STORE) kst[j + 1] = kbelow;
                 } else {
-                    const float2 Ej = layer_phase(kbelow, sm.d2[j + 1], sm.ea[j + 1]);
+                    const float2 Ej = layer_phase(kbelow, sm.lay[j + 1]);
                     const float2 Yj = cmul(Xbelow, Ej);
                     float2 Dj;
                     Xj = mobius(rj, Yj, Dj);
@@ -852,11 +881,13 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 float2 kbar = make_float2(0.f, 0.f); // adjoint of k_j (j >= 1)
                 Kz kj;
                 kj.re = k0h; kj.im = 0.f; kj.lo = k0l;
-                Kz kjm1 = kj;                          // k_{j-1}
                 float2 Xb_up = make_float2(0.f, 0.f);  // adjoint of X_{j-1}
+                Kz kjm1 = kj;                          // k_{j-1} (unrolled queue entries)
                 const float edge_u = kEdgeFrac * k0h * k0h;
                 auto adj_step = [&](int j, auto TOP, auto BOT) __attribute__((always_inline)) {
                     const bool top = pos_flag(TOP, j == 0), bot = pos_flag(BOT, j == n);
+                    const float4 Ij = sm.itf[j];
+                    const float4 Lj1 = sm.lay[j + 1]; // layer j+1 (zeros past the last layer)
                     const float2 Xb_in = Xb;
                     float2 Zj = make_float2(0.f, 0.f);
                     Kz kj1;
@@ -866,10 +897,10 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         rj = rst[j];
                         Gj = Gst[j];
                     } else {
-                        kj1 = bot ? medium_kz<false>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1])
-                                  : medium_kz<true>(p_hi, p_lo, sm.c[j + 1], sm.a[j + 1]);
-                        rj = top ? fresnel_nc<true>(kc(kj), kc(kj1), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj)
-                                 : fresnel_nc<false>(kc(kj), kc(kj1), sm.N[j], sm.s[j], sm.sl[j], Gj, kkj);
+                        const float4 Mj1 = sm.med[j + 1];
+                        kj1 = bot ? medium_kz<false>(p_hi, p_lo, Mj1) : medium_kz<true>(p_hi, p_lo, Mj1);
+                        rj = top ? fresnel_nc<true>(kc(kj), kc(kj1), Ij, Gj, kkj)
+                                 : fresnel_nc<false>(kc(kj), kc(kj1), Ij, Gj, kkj);
                     }
                     float2 kbar1 = make_float2(0.f, 0.f);
                     float2 rb;
@@ -881,7 +912,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                             Dj = Dst[j];
                             Y = Yst[j];
                         } else {
-                            Ej1 = layer_phase(kj1, sm.d2[j + 1], sm.ea[j + 1]);
+                            Ej1 = layer_phase(kj1, Lj1);
                             Y = cmul(X1, Ej1);
                             const float2 rY = cmul(rj, Y);
                             const float dx = 1.f + rY.x, dy = rY.y;
@@ -900,7 +931,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         // Re(k) Im(U) - Im(k) Re(U) (halved) and kbar_{j+1} = -2 i d U.
                         const float2 U = cmulc(Y, Yb);
                         acc_fma2(oD + j, kj1.re, U.y, -kj1.im, U.x);
-                        const float dd = sm.d2[j + 1].x;
+                        const float dd = Lj1.x;
                         kbar1 = make_float2(dd * U.y, -dd * U.x);
                     } else {
                         rb = Xb;
@@ -909,7 +940,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     // P = 2G + s r, M = s r - 2G.  With rr = conj(rbar) r
                     // (also the roughness term) and g = conj(G) rbar:
                     // conj(M) rbar = s conj(rr) - 2g, conj(P) rbar = s conj(rr) + 2g
-                    const float sj = sm.s[j];
+                    const float sj = Ij.z;
                     const float2 rr = cmulc(rb, rj);             // accS += Re(rr k_j k_{j+1})
                     const float2 gg = cmulc(Gj, rb);
                     const float2 sr = make_float2(sj * rr.x, -sj * rr.y);
@@ -932,11 +963,17 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         if (em) {
                             if (edge) {
                                 const int slot = eq_cnt + __popc(em & ((1u << lane) - 1u));
-                                sh_eq[warp][0][slot] = kc(kjm1);
-                                sh_eq[warp][1][slot] = kc(kj);
-                                sh_eq[warp][2][slot] = kc(kj1);
-                                sh_eq[warp][3][slot] = Zj;
-                                sh_eq[warp][4][slot] = Xb_up;
+                                if constexpr (T::SMEM_ACC) {
+                                    sh_eq[warp][0][slot] = make_float2(k0h, k0l);
+                                    sh_eq[warp][1][slot] = Zj;
+                                    sh_eq[warp][2][slot] = Xb_up;
+                                } else {
+                                    sh_eq[warp][0][slot] = kc(kjm1);
+                                    sh_eq[warp][1][slot] = kc(kj);
+                                    sh_eq[warp][2][slot] = kc(kj1);
+                                    sh_eq[warp][3][slot] = Zj;
+                                    sh_eq[warp][4][slot] = Xb_up;
+                                }
                                 sh_eqj[warp][slot] = j;
                             }
                             eq_cnt += __popc(em);
