@@ -61,6 +61,7 @@ def _lib(precision: str = "double") -> ctypes.CDLL:
             lib.oracle_reflectivity_unsmeared_d.argtypes = [c_int, D, c_int, D, c_int, D, D]
             lib.oracle_model.argtypes = [c_int, D, c_int, D, D, c_int, c_int, D]
             lib.oracle_loglik_grad.argtypes = [c_int, D, c_int, D, D, D, D, c_int, D, D]
+            lib.oracle_loglik_grad_res.argtypes = [c_int, D, c_int, D, D, D, D, c_int, D]
             lib.oracle_batch.argtypes = [c_int, c_int, I32, D, I32, c_int, I64, D, D, D, D,
                                          c_int, c_int, D, D, D]
             _LIBS[precision] = lib
@@ -133,10 +134,21 @@ def loglik_grad(n: int, params, Q, dQ, Robs, err, K: int, grad: bool = True,
     return float(ll[0]), g
 
 
+def loglik_grad_res(n: int, params, Q, dQ, Robs, err, K: int, precision: str = "double") -> float:
+    """d loglik / d ln f of one stack, where every dQ_i is scaled by f (at
+    f = 1): the derivative in a shared resolution (smearing) scale."""
+    p, Q, dQ, Robs, err = _f64(params), _f64(Q), _f64(dQ), _f64(Robs), _f64(err)
+    out = np.zeros(1)
+    _check(_lib(precision).oracle_loglik_grad_res(n, _d(p), Q.size, _d(Q), _d(dQ), _d(Robs), _d(err), K,
+                                                  _d(out)), "loglik_grad_res")
+    return float(out[0])
+
+
 def batch(mode: str, n_layers, params, dataset, q_off, Q, dQ, Robs, err, K: int,
           n_threads: int = 0, precision: str = "double"):
     """Batch driver.  mode: 'model' -> m [sum of dataset lengths over stacks];
-    'loglik' -> ll [n_stacks]; 'grad' -> (ll, grad packed like params)."""
+    'loglik' -> ll [n_stacks]; 'grad' -> (ll, grad packed like params);
+    'grad_res' -> (ll, grad, d ll / d ln(resolution scale) [n_stacks])."""
     nl = np.ascontiguousarray(n_layers, dtype=np.int32)
     ds = np.ascontiguousarray(dataset, dtype=np.int32)
     qo = np.ascontiguousarray(q_off, dtype=np.int64)
@@ -145,10 +157,10 @@ def batch(mode: str, n_layers, params, dataset, q_off, Q, dQ, Robs, err, K: int,
     err = _f64(err if err is not None else np.ones_like(Q))
     S = nl.size
     lens = (qo[1:] - qo[:-1])[ds] if S else np.zeros(0, np.int64)
-    m = np.zeros(int(lens.sum()) if mode == "model" else 1)
+    m = np.zeros(int(lens.sum()) if mode == "model" else max(S, 1) if mode == "grad_res" else 1)
     ll = np.zeros(max(S, 1))
-    g = np.zeros(p.size if mode == "grad" else 1)
-    code = {"model": 0, "loglik": 1, "grad": 2}[mode]
+    g = np.zeros(p.size if mode in ("grad", "grad_res") else 1)
+    code = {"model": 0, "loglik": 1, "grad": 2, "grad_res": 3}[mode]
     st = _lib(precision).oracle_batch(
         code, S, nl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _d(p),
         ds.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(qo.size - 1),
@@ -159,4 +171,6 @@ def batch(mode: str, n_layers, params, dataset, q_off, Q, dQ, Robs, err, K: int,
         return m
     if mode == "loglik":
         return ll[:S]
+    if mode == "grad_res":
+        return ll[:S], g, m[:S]
     return ll[:S], g

@@ -27,7 +27,12 @@
  *      loglik = -1/2 sum_i [ ((m_i - R_i)/e_i)^2 + ln(2 pi e_i^2) ];
  *  - the gradient of loglik w.r.t. every packed parameter, by forward-mode
  *    dual numbers (one pass per parameter), the exact derivative the paper
- *    obtains by automatic differentiation (Sec. 2.1, Fig. 1; Sec. 3).
+ *    obtains by automatic differentiation (Sec. 2.1, Fig. 1; Sec. 3);
+ *  - the derivative of loglik w.r.t. the resolution, taken as a common scale
+ *    f of every dQ_i (dQ_i -> f dQ_i, derivative in ln f at f = 1): the
+ *    quantity a fit of a shared smearing percentage needs (Sec. 4.2, the
+ *    LED fit's smearing parameter); one more dual pass, seeded on the node
+ *    positions, dq_k / d ln f = sqrt(2) sigma_Q x_k.
  *
  * Readings where the paper is silent (the paper prints no reflectivity
  * equation):
@@ -156,12 +161,13 @@ static void unpack(int n, const double *p, int seed, stack_t_ *s)
 #undef NEXT
 }
 
-/* z-components of the wavevector in every medium at momentum transfer q. */
-static void wavevectors(const stack_t_ *s, real q, dual *k)
+/* z-components of the wavevector in every medium at momentum transfer q
+ * (with tangent qt: q itself may carry the derivative direction). */
+static void wavevectors(const stack_t_ *s, real q, real qt, dual *k)
 {
     const int n = s->n;
-    real k0 = q / 2;
-    k[0] = dconst(k0);
+    real k0 = q / 2, k0t = qt / 2;
+    k[0] = dl(k0, k0t);
     for (int j = 1; j <= n + 1; ++j) {
         /* k0^2 - 4 pi (rho_j - rho_0) + 4 pi i iota_j ; adding +0.0 to the
          * imaginary part turns a -0.0 into +0.0 so that csqrt stays on the
@@ -170,7 +176,7 @@ static void wavevectors(const stack_t_ *s, real q, dual *k)
         cplx re_v = k0 * k0 - 4 * R_PI * C_RE(drho.v);
         real im_v = 4 * R_PI * C_RE(s->iota[j].v) + (real)0.0;
         cplx v = re_v + im_v * I;
-        cplx t = -4 * R_PI * drho.t + 4 * R_PI * s->iota[j].t * I;
+        cplx t = 2 * k0 * k0t - 4 * R_PI * drho.t + 4 * R_PI * s->iota[j].t * I;
         k[j] = dsqrt(dl(v, t));
     }
 }
@@ -191,12 +197,12 @@ static dual fresnel(const stack_t_ *s, const dual *k, int j)
 /* Complex reflection amplitude of the stack at q.
  * form 0: Abeles characteristic-matrix product (the definition);
  * form 1: Parratt recursion from the backing upwards (cross-check). */
-static dual amplitude(const stack_t_ *s, real q, int form)
+static dual amplitude(const stack_t_ *s, real q, real qt, int form)
 {
     const int n = s->n;
     dual k[ORACLE_MAX_LAYERS + 2];
     dual r[ORACLE_MAX_LAYERS + 1];
-    wavevectors(s, q, k);
+    wavevectors(s, q, qt, k);
     for (int j = 0; j <= n; ++j) r[j] = fresnel(s, k, j);
 
     if (form == 0) {
@@ -295,19 +301,22 @@ static int make_quad(int K, quad_t_ *qd)
     return gauss_hermite(K, qd->x, qd->w);
 }
 
-/* m(Q) = scale * S(Q) + bkg as a real-valued dual. */
-static int smeared_model(const stack_t_ *s, real Q, real dQ, const quad_t_ *qd, int form, dual *m)
+/* m(Q) = scale * S(Q) + bkg as a real-valued dual.  res_seed: the tangent
+ * is the derivative in ln f of the resolution scale f (dQ -> f dQ, f = 1). */
+static int smeared_model(const stack_t_ *s, real Q, real dQ, const quad_t_ *qd, int form, int res_seed,
+                         dual *m)
 {
     dual S = dconst(0);
     if (dQ == 0) {
         if (!(Q > 0)) return OR_EDOMAIN;
-        S = dabs2(amplitude(s, Q, form));
+        S = dabs2(amplitude(s, Q, 0, form));
     } else {
         real sigQ = dQ / (2 * R_SQRT(2 * R_LN2));
         for (int k = 0; k < qd->K; ++k) {
-            real qk = Q + R_SQRT((real)2) * sigQ * qd->x[k];
+            real step = R_SQRT((real)2) * sigQ * qd->x[k];
+            real qk = Q + step;
             if (!(qk > 0)) return OR_EDOMAIN;
-            dual R = dabs2(amplitude(s, qk, form));
+            dual R = dabs2(amplitude(s, qk, res_seed ? step : 0, form));
             S = dadd(S, dscale(R, qd->w[k] / R_SQRT(R_PI)));
         }
     }
@@ -316,13 +325,13 @@ static int smeared_model(const stack_t_ *s, real Q, real dQ, const quad_t_ *qd, 
 }
 
 static int loglik_dual(const stack_t_ *s, int nq, const double *Q, const double *dQ,
-                       const double *Robs, const double *err, const quad_t_ *qd, dual *ll)
+                       const double *Robs, const double *err, const quad_t_ *qd, int res_seed, dual *ll)
 {
     dual acc = dconst(0);
     for (int i = 0; i < nq; ++i) {
         if (!(err[i] > 0)) return OR_EDOMAIN;
         dual m;
-        int st = smeared_model(s, Q[i], dQ[i], qd, 0, &m);
+        int st = smeared_model(s, Q[i], dQ[i], qd, 0, res_seed, &m);
         if (st) return st;
         real e = err[i];
         dual res = dscale(dsub(m, dconst(Robs[i])), 1 / e);
@@ -375,7 +384,7 @@ int oracle_amplitude(int n, const double *params, int nq, const double *q, int f
     unpack(n, params, -1, &s);
     for (int i = 0; i < nq; ++i) {
         if (!(q[i] > 0)) return OR_EDOMAIN;
-        dual r = amplitude(&s, q[i], form);
+        dual r = amplitude(&s, q[i], 0, form);
         re[i] = (double)C_RE(r.v);
         im[i] = (double)C_IM(r.v);
     }
@@ -392,7 +401,7 @@ int oracle_reflectivity_unsmeared_d(int n, const double *params, int nq, const d
     unpack(n, params, seed, &s);
     for (int i = 0; i < nq; ++i) {
         if (!(q[i] > 0)) return OR_EDOMAIN;
-        dual v = dabs2(amplitude(&s, q[i], 0));
+        dual v = dabs2(amplitude(&s, q[i], 0, 0));
         R[i] = (double)C_RE(v.v);
         if (dR) dR[i] = (double)C_RE(v.t);
     }
@@ -410,7 +419,7 @@ int oracle_model(int n, const double *params, int nq, const double *Q, const dou
     unpack(n, params, -1, &s);
     for (int i = 0; i < nq; ++i) {
         dual v;
-        int st = smeared_model(&s, Q[i], dQ[i], &qd, form, &v);
+        int st = smeared_model(&s, Q[i], dQ[i], &qd, form, 0, &v);
         if (st) return st;
         m[i] = (double)C_RE(v.v);
     }
@@ -428,13 +437,13 @@ int oracle_loglik_grad(int n, const double *params, int nq, const double *Q, con
     stack_t_ s;
     dual v;
     unpack(n, params, -1, &s);
-    int st = loglik_dual(&s, nq, Q, dQ, Robs, err, &qd, &v);
+    int st = loglik_dual(&s, nq, Q, dQ, Robs, err, &qd, 0, &v);
     if (st) return st;
     *ll = (double)C_RE(v.v);
     if (grad) {
         for (int p = 0; p < 4 * n + 6; ++p) {
             unpack(n, params, p, &s);
-            st = loglik_dual(&s, nq, Q, dQ, Robs, err, &qd, &v);
+            st = loglik_dual(&s, nq, Q, dQ, Robs, err, &qd, 0, &v);
             if (st) return st;
             grad[p] = (double)C_RE(v.t);
         }
@@ -442,10 +451,28 @@ int oracle_loglik_grad(int n, const double *params, int nq, const double *Q, con
     return OR_OK;
 }
 
+/* d loglik / d ln f of one stack, f a common scale of every dQ_i (f = 1). */
+int oracle_loglik_grad_res(int n, const double *params, int nq, const double *Q, const double *dQ,
+                           const double *Robs, const double *err, int K, double *gres)
+{
+    if (check_stack(n, params)) return OR_EINVAL;
+    quad_t_ qd;
+    if (make_quad(K, &qd)) return OR_EINVAL;
+    stack_t_ s;
+    dual v;
+    unpack(n, params, -1, &s);
+    int st = loglik_dual(&s, nq, Q, dQ, Robs, err, &qd, 1, &v);
+    if (st) return st;
+    *gres = (double)C_RE(v.t);
+    return OR_OK;
+}
+
 /* Batch driver over many stacks (OpenMP over stacks when available).
  * mode 0: smeared model into out_m (offsets: prefix over stacks of the
  *         dataset lengths); mode 1: loglik; mode 2: loglik and gradient
- *         (packed like params).  Returns 0, or the first failing status. */
+ *         (packed like params); mode 3: loglik, gradient and, in out_m (one
+ *         value per stack), d loglik / d ln f of the resolution scale.
+ *         Returns 0, or the first failing status. */
 int oracle_batch(int mode, int n_stacks, const int32_t *n_layers, const double *params,
                  const int32_t *dataset, int n_datasets, const int64_t *q_off,
                  const double *Q, const double *dQ, const double *Robs, const double *err,
@@ -480,7 +507,9 @@ int oracle_batch(int mode, int n_stacks, const int32_t *n_layers, const double *
             st = oracle_model(n, p, nq, Q + q0, dQ + q0, K, 0, out_m + out_off[s]);
         } else {
             st = oracle_loglik_grad(n, p, nq, Q + q0, dQ + q0, Robs + q0, err + q0, K,
-                                    out_ll + s, mode == 2 ? out_grad + par_off[s] : NULL);
+                                    out_ll + s, mode >= 2 ? out_grad + par_off[s] : NULL);
+            if (!st && mode == 3)
+                st = oracle_loglik_grad_res(n, p, nq, Q + q0, dQ + q0, Robs + q0, err + q0, K, out_m + s);
         }
         if (st) {
 #ifdef _OPENMP

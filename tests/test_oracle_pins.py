@@ -317,3 +317,70 @@ def test_batch_driver_matches_single_stack_calls():
         assert ll[s] == l1
         po = wl.par_off
         np.testing.assert_array_equal(g[po[s]:po[s + 1]], g1)
+
+
+# ------------------------------------------------ resolution (smearing) scale
+def test_resolution_derivative_fresnel_closed_form():
+    """d loglik / d ln f (every dQ_i -> f dQ_i) for a bare rough-free
+    substrate, written out here from the Fresnel amplitude: with k_0 = q/2,
+    k_1 = sqrt(k_0^2 - 4 pi drho), dr/dk_0 = -8 pi drho / (k_1 (k_0 + k_1)^2),
+    dR/dq = Re(conj(r) dr/dk_0) and dq_k/d ln f = sqrt(2) sigma_Q x_k."""
+    drho, scale, bkg, K = 2.07e-6, 0.97, 2e-7, 17
+    p = W.pack([], [0.0, drho], [0.0], [0.0], scale, bkg)
+    Q = W.log_grid(80, 0.005, 0.3).astype(np.float64)   # spans the critical edge
+    dQ = 0.05 * Q
+    rng = np.random.default_rng(5)
+    m = oracle.model(0, p, Q, dQ, K)
+    Robs = m * np.exp(rng.normal(0, 0.05, m.size))
+    err = 0.05 * m
+    x, w = np.polynomial.hermite.hermgauss(K)
+    sig = dQ / (2 * np.sqrt(2 * np.log(2)))
+    q = Q[:, None] + np.sqrt(2) * sig[:, None] * x[None, :]
+    k0 = q / 2
+    k1 = np.sqrt(k0 ** 2 - FOURPI * drho + 0j)
+    r = (k0 - k1) / (k0 + k1)
+    dr = -2 * FOURPI * drho / (k1 * (k0 + k1) ** 2)
+    dR = np.real(np.conj(r) * dr)
+    S = (w / np.sqrt(np.pi) * np.abs(r) ** 2).sum(axis=1)
+    dS = (w / np.sqrt(np.pi) * dR * np.sqrt(2) * sig[:, None] * x[None, :]).sum(axis=1)
+    mm = scale * S + bkg
+    ref = np.sum(-(mm - Robs) / err ** 2 * scale * dS)
+    got = oracle.loglik_grad_res(0, p, Q, dQ, Robs, err, K)
+    assert abs(got - ref) <= 1e-9 * np.sum(np.abs((mm - Robs) / err ** 2 * scale * dS))
+
+
+@pytest.mark.parametrize("n", [1, 3])
+def test_resolution_derivative_matches_central_differences(n):
+    rng = np.random.default_rng(23 + n)
+    p = W.pack(rng.uniform(60, 900, n), np.concatenate([[0.0], rng.uniform(1e-6, 6e-6, n), [2.07e-6]]),
+               np.concatenate([rng.uniform(1e-9, 1e-8, n), [0.0]]), rng.uniform(2, 12, n + 1), 1.01, 1e-7)
+    Q = W.log_grid(70, 0.005, 0.25).astype(np.float64)
+    dQ = rng.uniform(0.02, 0.08, Q.size) * Q
+    m = oracle.model(n, p, Q, dQ, 21)
+    Robs = m * np.exp(rng.normal(0, 0.05, m.size))
+    err = 0.05 * m
+    g = oracle.loglik_grad_res(n, p, Q, dQ, Robs, err, 21)
+    h = 1e-5
+    fp, _ = oracle.loglik_grad(n, p, Q, dQ * np.exp(h), Robs, err, 21, grad=False, precision="long")
+    fm, _ = oracle.loglik_grad(n, p, Q, dQ * np.exp(-h), Robs, err, 21, grad=False, precision="long")
+    assert abs(g - (fp - fm) / (2 * h)) <= 1e-7 * abs(g)
+
+
+def test_resolution_derivative_vanishes_without_smearing():
+    p = one_layer(250.0, 4.5e-6, 1e-9, [4.0, 6.0], scale=1.0, bkg=1e-7)
+    Q = W.log_grid(40, 0.006, 0.2).astype(np.float64)
+    m = oracle.model(1, p, Q, np.zeros_like(Q), 17)
+    assert oracle.loglik_grad_res(1, p, Q, np.zeros_like(Q), m * 1.03, 0.05 * m, 17) == 0.0
+
+
+def test_batch_resolution_mode_matches_single_stack_calls():
+    wl = W.make_workload("uneven", n_stacks=3)
+    ll, g = oracle.batch("grad", wl.n_layers, wl.params, wl.dataset, wl.q_off, wl.q, wl.dq,
+                         wl.r_obs, wl.r_err, wl.n_quad)
+    ll3, g3, gr = oracle.batch("grad_res", wl.n_layers, wl.params, wl.dataset, wl.q_off, wl.q, wl.dq,
+                               wl.r_obs, wl.r_err, wl.n_quad)
+    np.testing.assert_array_equal(ll, ll3)
+    np.testing.assert_array_equal(g, g3)
+    for s in range(wl.n_stacks):
+        Q, dQ, Ro, e = wl.dataset_arrays(int(wl.dataset[s]))
+        assert gr[s] == oracle.loglik_grad_res(int(wl.n_layers[s]), wl.stack_params(s), Q, dQ, Ro, e, wl.n_quad)
