@@ -151,6 +151,20 @@ nr_status nr_loglik(nr_ctx *ctx, const nr_batch *batch, double *loglik, void *st
 nr_status nr_loglik_grad(nr_ctx *ctx, const nr_batch *batch, double *loglik, double *grad,
                          void *stream);
 
+/* nr_loglik_grad plus the derivative of each stack's log-likelihood in a
+ * shared resolution scale: every dQ_i of the stack's dataset is taken as
+ * f * dQ_i and grad_res[s] = d loglik_s / d ln f at f = 1.  A fit that
+ * infers a common smearing percentage (the LED co-fit's resolution
+ * parameter, Sec. 4.2) needs it: with dQ_i = f Q_i, d loglik / d f =
+ * grad_res / f.  The adjoint carries it through the quadrature nodes,
+ * dq_k / d ln f = dQ_i x_k / (2 sqrt(ln 2)) (Gaussian smearing of Sec. 3).
+ *   grad_res: [S] doubles, same memory kind as the batch; loglik and grad as
+ *             for nr_loglik_grad (either may be NULL).
+ * NR_MIXED only: a context created with NR_FP64_PLAIN returns NR_EINVAL.
+ * Other errors as for nr_loglik_grad. */
+nr_status nr_loglik_grad_res(nr_ctx *ctx, const nr_batch *batch, double *loglik, double *grad,
+                             double *grad_res, void *stream);
+
 /* Synchronise `stream`, return the sticky device flags raised since the
  * last call (NR_FLAG_*) in *flags and clear them.  Returns NR_ENONFINITE
  * when any flag was set, NR_OK otherwise. */

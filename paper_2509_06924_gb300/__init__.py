@@ -33,7 +33,8 @@ NR_FLAG_NONFINITE_PARAM, NR_FLAG_BAD_Q, NR_FLAG_BAD_ERR = 1, 2, 4
 MAX_LAYERS = 64
 MAX_QUAD = 32
 EXPORTS = ("nr_create", "nr_destroy", "nr_last_error", "nr_plan", "nr_reflectivity", "nr_loglik",
-           "nr_loglik_grad", "nr_device_status", "nr_quadrature", "nr_plan_info", "nr_loglik_grad_noalloc")
+           "nr_loglik_grad", "nr_loglik_grad_res", "nr_device_status", "nr_quadrature", "nr_plan_info",
+           "nr_loglik_grad_noalloc")
 NOALLOC_MAX_STACKS = 16384
 
 
@@ -270,6 +271,19 @@ class Context:
         _check(self._lib.nr_loglik_grad(self._h, ctypes.byref(cb), ctypes.c_void_p(ll.data_ptr()),
                                         ctypes.c_void_p(g.data_ptr()), _stream_handle(stream)))
         return ll, g
+
+    def loglik_grad_res(self, batch: Batch, ll_out=None, grad_out=None, res_out=None, stream=None):
+        """(loglik [S], gradient packed like params, d loglik / d ln f [S]),
+        float64, f a common scale of every dQ of a stack's dataset (f = 1)."""
+        import torch
+        ll = self._alloc(batch, batch.n_stacks, torch.float64, ll_out)
+        g = self._alloc(batch, batch.params.numel(), torch.float64, grad_out)
+        r = self._alloc(batch, batch.n_stacks, torch.float64, res_out)
+        cb = batch._c()
+        _check(self._lib.nr_loglik_grad_res(self._h, ctypes.byref(cb), ctypes.c_void_p(ll.data_ptr()),
+                                            ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(r.data_ptr()),
+                                            _stream_handle(stream)))
+        return ll, g, r
 
     def device_status(self, stream=None) -> int:
         """Synchronise and return (and clear) the sticky NR_FLAG_* word."""

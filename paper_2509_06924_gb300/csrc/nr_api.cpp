@@ -199,7 +199,7 @@ struct nr_ctx {
     std::vector<std::unique_ptr<Plan>> plans;
     uint64_t clock = 0;
     // host-memory staging
-    DevBuf s_params, s_q, s_dq, s_robs, s_rerr, s_out, s_ll, s_grad;
+    DevBuf s_params, s_q, s_dq, s_robs, s_rerr, s_out, s_ll, s_grad, s_res;
 };
 
 namespace {
@@ -268,7 +268,7 @@ nr_status build_worklist(nr_ctx *ctx, Plan &pl, int mode, WorkList &wl)
     const int S = pl.S;
     std::vector<int> bucket(S);
     for (int s = 0; s < S; ++s)
-        bucket[s] = mode == kGrad ? grad_bucket(pl.n_layers[s]) : fwd_bucket(pl.n_layers[s]);
+        bucket[s] = is_grad_mode(mode) ? grad_bucket(pl.n_layers[s]) : fwd_bucket(pl.n_layers[s]);
     std::vector<int> order(S);
     for (int s = 0; s < S; ++s) order[s] = s;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bucket[a] < bucket[b]; });
@@ -330,7 +330,7 @@ nr_status build_worklist(nr_ctx *ctx, Plan &pl, int mode, WorkList &wl)
             si.n_chunks = nch;
             si.part_base = nch > 1 ? part : 0;
             si.pad = 0;
-            if (nch > 1) part += (int64_t)nch * (4 * si.n + 6);
+            if (nch > 1) part += (int64_t)nch * n_slot(si.n);
             for (int c = 0; c < nch; ++c) {
                 WorkItem w;
                 w.stack = s;
@@ -448,7 +448,7 @@ nr_status get_plan(nr_ctx *ctx, const nr_batch *b, int mode, Plan **out)
         nr_status st = NR_OK;
         if (ctx->opt.precision == NR_FP64_PLAIN) {
             if (!pl->fp64_built) { st = build_fp64(ctx, *pl); pl->fp64_built = st == NR_OK; }
-        } else if (mode == kGrad) {
+        } else if (is_grad_mode(mode)) {
             if (!pl->grad_built) { st = build_worklist(ctx, *pl, kGrad, pl->grad); pl->grad_built = st == NR_OK; }
         } else {
             if (!pl->fwd_built) { st = build_worklist(ctx, *pl, kModel, pl->fwd); pl->fwd_built = st == NR_OK; }
@@ -460,7 +460,7 @@ nr_status get_plan(nr_ctx *ctx, const nr_batch *b, int mode, Plan **out)
 }
 
 nr_status launch_device(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, float *r_out, double *ll,
-                        double *grad, cudaStream_t st)
+                        double *grad, double *gres, cudaStream_t st)
 {
     if (pl.S == 0) return NR_OK;
     KernelArgs a{};
@@ -472,6 +472,7 @@ nr_status launch_device(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, floa
     a.r_out = r_out;
     a.ll_out = ll;
     a.grad_out = grad;
+    a.res_out = gres;
     a.status = ctx->d_status;
     if (ctx->opt.precision == NR_FP64_PLAIN) {
         a.stacks = pl.d64_stacks.as<StackInfo>();
@@ -484,7 +485,7 @@ nr_status launch_device(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, floa
         if (e != cudaSuccess) return fail(NR_ECUDA, "fp64 launch: %s", cudaGetErrorString(e));
         return NR_OK;
     }
-    WorkList &wl = mode == kGrad ? pl.grad : pl.fwd;
+    WorkList &wl = is_grad_mode(mode) ? pl.grad : pl.fwd;
     a.stacks = wl.d_stacks.as<StackInfo>();
     a.partials = wl.d_partials.as<double>();
     a.stack_done = wl.d_done.as<int32_t>();
@@ -502,7 +503,7 @@ nr_status launch_device(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, floa
 
 // Host-memory batches: copy in, compute, copy out, synchronise.
 nr_status run_host(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, float *r_out, double *ll, double *grad,
-                   cudaStream_t st)
+                   double *gres, cudaStream_t st)
 {
     if (pl.S == 0) return NR_OK;
     const size_t np = sizeof(double) * pl.total_params, nqb = sizeof(float) * pl.total_q;
@@ -530,20 +531,23 @@ nr_status run_host(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, float *r_
     db.r_obs = need_data ? ctx->s_robs.as<float>() : nullptr;
     db.r_err = need_data ? ctx->s_rerr.as<float>() : nullptr;
     float *d_out = nullptr;
-    double *d_ll = nullptr, *d_grad = nullptr;
+    double *d_ll = nullptr, *d_grad = nullptr, *d_res = nullptr;
     if (r_out) { NR_CUDA(ctx->s_out.ensure(sizeof(float) * pl.total_out)); d_out = ctx->s_out.as<float>(); }
     if (ll) { NR_CUDA(ctx->s_ll.ensure(sizeof(double) * pl.S)); d_ll = ctx->s_ll.as<double>(); }
     if (grad) { NR_CUDA(ctx->s_grad.ensure(np)); d_grad = ctx->s_grad.as<double>(); }
-    nr_status s = launch_device(ctx, pl, &db, mode, d_out, d_ll, d_grad, st);
+    if (gres) { NR_CUDA(ctx->s_res.ensure(sizeof(double) * pl.S)); d_res = ctx->s_res.as<double>(); }
+    nr_status s = launch_device(ctx, pl, &db, mode, d_out, d_ll, d_grad, d_res, st);
     if (s != NR_OK) return s;
     if (r_out) NR_CUDA(cudaMemcpyAsync(r_out, d_out, sizeof(float) * pl.total_out, cudaMemcpyDeviceToHost, st));
     if (ll) NR_CUDA(cudaMemcpyAsync(ll, d_ll, sizeof(double) * pl.S, cudaMemcpyDeviceToHost, st));
     if (grad) NR_CUDA(cudaMemcpyAsync(grad, d_grad, np, cudaMemcpyDeviceToHost, st));
+    if (gres) NR_CUDA(cudaMemcpyAsync(gres, d_res, sizeof(double) * pl.S, cudaMemcpyDeviceToHost, st));
     NR_CUDA(cudaStreamSynchronize(st));
     return NR_OK;
 }
 
-nr_status compute(nr_ctx *ctx, const nr_batch *b, int mode, float *r_out, double *ll, double *grad, void *stream)
+nr_status compute(nr_ctx *ctx, const nr_batch *b, int mode, float *r_out, double *ll, double *grad, double *gres,
+                  void *stream)
 {
     if (!ctx) return fail(NR_EINVAL, "context is NULL");
     if (!b) return fail(NR_EINVAL, "batch is NULL");
@@ -551,13 +555,15 @@ nr_status compute(nr_ctx *ctx, const nr_batch *b, int mode, float *r_out, double
     if (mode == kLoglik && !ll && b->n_stacks > 0) return fail(NR_EINVAL, "loglik is NULL");
     if (mode != kModel && b->n_stacks > 0 && (!b->r_obs || !b->r_err))
         return fail(NR_EINVAL, "r_obs/r_err are required for the likelihood");
+    if (mode == kGradRes && ctx->opt.precision != NR_MIXED)
+        return fail(NR_EINVAL, "the resolution derivative is computed by the NR_MIXED path only");
     NR_CUDA(cudaSetDevice(ctx->device));
     Plan *pl = nullptr;
     nr_status st = get_plan(ctx, b, mode, &pl);
     if (st != NR_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (b->memory == NR_MEM_HOST) return run_host(ctx, *pl, b, mode, r_out, ll, grad, s);
-    return launch_device(ctx, *pl, b, mode, r_out, ll, grad, s);
+    if (b->memory == NR_MEM_HOST) return run_host(ctx, *pl, b, mode, r_out, ll, grad, gres, s);
+    return launch_device(ctx, *pl, b, mode, r_out, ll, grad, gres, s);
 }
 
 } // namespace
@@ -628,17 +634,23 @@ nr_status nr_plan(nr_ctx *ctx, const nr_batch *batch)
 
 nr_status nr_reflectivity(nr_ctx *ctx, const nr_batch *batch, float *r_out, void *stream)
 {
-    return compute(ctx, batch, kModel, r_out, nullptr, nullptr, stream);
+    return compute(ctx, batch, kModel, r_out, nullptr, nullptr, nullptr, stream);
 }
 
 nr_status nr_loglik(nr_ctx *ctx, const nr_batch *batch, double *loglik, void *stream)
 {
-    return compute(ctx, batch, kLoglik, nullptr, loglik, nullptr, stream);
+    return compute(ctx, batch, kLoglik, nullptr, loglik, nullptr, nullptr, stream);
 }
 
 nr_status nr_loglik_grad(nr_ctx *ctx, const nr_batch *batch, double *loglik, double *grad, void *stream)
 {
-    return compute(ctx, batch, kGrad, nullptr, loglik, grad, stream);
+    return compute(ctx, batch, kGrad, nullptr, loglik, grad, nullptr, stream);
+}
+
+nr_status nr_loglik_grad_res(nr_ctx *ctx, const nr_batch *batch, double *loglik, double *grad, double *grad_res,
+                             void *stream)
+{
+    return compute(ctx, batch, kGradRes, nullptr, loglik, grad, grad_res, stream);
 }
 
 nr_status nr_device_status(nr_ctx *ctx, void *stream, int32_t *flags)

@@ -10,7 +10,9 @@
 
 namespace nrimpl {
 
-enum Mode : int { kModel = 0, kLoglik = 1, kGrad = 2 };
+// kGradRes: kGrad plus d loglik / d ln(resolution scale) per stack
+enum Mode : int { kModel = 0, kLoglik = 1, kGrad = 2, kGradRes = 3 };
+__host__ __device__ inline bool is_grad_mode(int mode) { return mode == kGrad || mode == kGradRes; }
 
 // Lanes that share one Q point's smearing sum in the mixed kernels; a tile
 // therefore holds at most (threads per CTA) / kSubLanes Q points.
@@ -62,6 +64,7 @@ struct KernelArgs {
     float *r_out;
     double *ll_out;
     double *grad_out;
+    double *res_out;     // [n_stacks] d loglik / d ln(dQ scale) (kGradRes)
     double *partials;    // per-chunk raw sums of chunked stacks
     int32_t *stack_done; // per-stack arrival counters (self-resetting)
     int32_t *ticket;     // [2]: next work item, finished CTAs (self-resetting)
@@ -88,8 +91,9 @@ constexpr int kFp64Block = 128;
 cudaError_t launch_fp64(int mode, const KernelArgs &a, const QuadConst &qc, cudaStream_t st);
 cudaError_t launch_fp64_finalize(int mode, int n_stacks, const KernelArgs &a, cudaStream_t st);
 
-// Number of raw per-stack sums the mixed gradient kernel produces
-// (= packed parameter count 4n+6).
-__host__ __device__ inline int n_raw(int n) { return 4 * n + 6; }
+// Raw per-stack sums of the mixed gradient kernels, and the stride of a
+// chunk's partial-sum slot: [accD (n) | accUr (n+1) | accUi (n+1) |
+// accS (n+1) | llsum | gscale | gbkg | gres].
+__host__ __device__ inline int n_slot(int n) { return 4 * n + 7; }
 
 } // namespace nrimpl

@@ -164,8 +164,6 @@ __device__ __forceinline__ float2 csqr(float2 a)
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
-// Re(conj(a) * b)
-__device__ __forceinline__ float redot(float2 a, float2 b) { return fmaf(a.x, b.x, a.y * b.y); }
 // 1 - a^2
 __device__ __forceinline__ float2 one_minus_sq(float2 a)
 {
@@ -427,23 +425,27 @@ __device__ __forceinline__ float2 edge_entry_ubar(float2 node, float2 Z, float2 
 // slot of medium 1's Re-accumulator; stride between accumulators `stride`,
 // Re -> Im distance `im_off`; med, lay: the staged stack entries).  Kept out
 // of line so that the rolled sweep it is called from keeps its register budget.
-template <int EQ>
-__device__ __noinline__ void eq_drain_smem(float2 (*q)[EQ], const int *qj, const float4 *med, const float4 *lay,
-                                           int n, int lane, int cnt, float *acc, int stride, int im_off)
+template <int EQ, bool RES>
+__device__ __noinline__ float eq_drain_smem(float2 (*q)[EQ], const int *qj, const float4 *med, const float4 *lay,
+                                            int n, int lane, int cnt, float *acc, int stride, int im_off)
 {
+    float res = 0.f; // the resolution-mode term of the entry (factor in q[3])
     if (lane < cnt) {
         const int j = qj[lane];
         const float2 ub = edge_entry_ubar(q[0][lane], q[1][lane], q[2][lane], j, n, med, lay);
         // conj(kbar)/k_j = 2 conj(ubar)
         acc[(j - 1) * stride] += 2.f * ub.x;
         acc[(j - 1) * stride + im_off] += -2.f * ub.y;
+        if constexpr (RES) res = 2.f * ub.x * q[3][lane].x;
     }
+    return res;
 }
 
 // --------------------------------------------------------------- traits ---
 template <int MODE, int NMAX>
 struct Traits {
-    static constexpr bool kGradMode = MODE == kGrad;
+    static constexpr bool kGradMode = MODE == kGrad || MODE == kGradRes;
+    static constexpr bool RES = MODE == kGradRes;               // + d loglik / d ln(dQ scale)
     static constexpr int NM = NMAX > 0 ? NMAX : NR_MAX_LAYERS; // smem capacity
     // deep gradient buckets run 128-thread CTAs so that their per-thread
     // state in shared memory still leaves room for several CTAs per SM
@@ -454,7 +456,7 @@ struct Traits {
     static constexpr bool SMEM_ACC = kGradMode && !UNROLL;    // partials in shared memory
     static constexpr bool X_SMEM = kGradMode && !UNROLL;      // X_j in shared memory
     static constexpr int NACC = kGradMode ? 4 * NM + 3 : 0;   // partial gradients per thread
-    static constexpr int NRAW = 4 * NM + 6;
+    static constexpr int NRAW = 4 * NM + 7;
     static constexpr int WARPS = BLOCK / 32;
     // interior-edge work queue per warp: unrolled kernels drain it after each
     // tile's sweep, rolled ones inside the sweep
@@ -536,13 +538,14 @@ __device__ void stage_stack(StackSmem<NM> &sm, const double *p, int n, int tid, 
 }
 
 // Convert a stack's raw sums into outputs (loglik, packed gradient).
-//   raw: [accD (n) | accUr (n+1) | accUi (n+1) | accS (n+1) | llsum | gscale | gbkg]
+//   raw: [accD (n) | accUr (n+1) | accUi (n+1) | accS (n+1) | llsum | gscale | gbkg | gres]
 template <int MODE>
 __device__ void finalize_stack(const double *raw, int n, const double *p, int s, int64_t par_off,
-                               double *ll_out, double *grad_out, int tid, int nthreads)
+                               double *ll_out, double *grad_out, double *res_out, int tid, int nthreads)
 {
     if (tid == 0 && ll_out) ll_out[s] = -0.5 * raw[4 * n + 3];
-    if (MODE != kGrad || grad_out == nullptr) return;
+    if (MODE == kGradRes && tid == 0 && res_out) res_out[s] = raw[4 * n + 6];
+    if (!is_grad_mode(MODE) || grad_out == nullptr) return;
     const double twoPi = 6.283185307179586476925286766559;
     double *g = grad_out + par_off;
     for (int i = tid; i < 4 * n + 6; i += nthreads) {
@@ -576,6 +579,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     constexpr int NM = T::NM;
     constexpr int BLOCK = T::BLOCK;
     constexpr bool GRAD = T::kGradMode;
+    constexpr bool RES = T::RES;
     constexpr bool LIK = MODE != kModel;
     constexpr int EQ = T::EQ_CAP;
 
@@ -592,8 +596,9 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     __shared__ int sh_last;
     // interior-edge queue per warp: k_{j-1}, k_j, k_{j+1}, Z, Xbar_{j-1} and
     // the medium j; the rolled sweeps keep the node k_0 in place of the three
-    // wavevectors (smaller entries, more CTAs per SM)
-    constexpr int EQF = T::SMEM_ACC ? 3 : 5;
+    // wavevectors (smaller entries, more CTAs per SM); the resolution mode
+    // adds the factor that turns the entry's conj(kbar)/k into d/d ln f
+    constexpr int EQF = (T::SMEM_ACC ? 3 : 5) + (RES ? 1 : 0); // RES: + k_0 dk_0/dln f
     __shared__ float2 sh_eq[GRAD ? T::WARPS : 1][EQF][EQ];
     __shared__ int sh_eqj[GRAD ? T::WARPS : 1][EQ];
     extern __shared__ __align__(16) float sh_dyn[]; // [NACC][BLOCK] partials, then [NM+1][BLOCK] X_j
@@ -676,12 +681,13 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 }
             }
         };
+        float gres_acc = 0.f; // per-thread d loglik / d ln(dQ scale) (RES)
         int eq_cnt = 0; // entries in this warp's interior-edge queue (warp-uniform)
         // drain `cnt` <= 32 queued entries, one per lane, then shift the rest down
         auto eq_drain = [&](int cnt) {
             if constexpr (T::SMEM_ACC) {
-                eq_drain_smem<EQ>(sh_eq[warp], sh_eqj[warp], sm.med, sm.lay, n, lane, cnt, sh_acc + oUr * BLOCK + tid,
-                                  BLOCK, (oUi - oUr) * BLOCK);
+                gres_acc += eq_drain_smem<EQ, RES>(sh_eq[warp], sh_eqj[warp], sm.med, sm.lay, n, lane, cnt,
+                                                   sh_acc + oUr * BLOCK + tid, BLOCK, (oUi - oUr) * BLOCK);
             } else if (lane < cnt) {
                 const int j = sh_eqj[warp][lane];
                 const float2 ub = edge_ubar(sh_eq[warp][0][lane], sh_eq[warp][1][lane], sh_eq[warp][2][lane],
@@ -689,6 +695,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                                             j == n, sh_eq[warp][4][lane]);
                 // conj(kbar)/k_j = 2 conj(ubar)
                 acc_u(j, make_float2(2.f * ub.x, -2.f * ub.y));
+                if constexpr (RES) gres_acc = fmaf(2.f * ub.x, sh_eq[warp][EQF - 1][lane].x, gres_acc);
             }
             __syncwarp();
             const int rest = eq_cnt - cnt;
@@ -884,6 +891,16 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 float2 Xb_up = make_float2(0.f, 0.f);  // adjoint of X_{j-1}
                 Kz kjm1 = kj;                          // k_{j-1} (unrolled queue entries)
                 const float edge_u = kEdgeFrac * k0h * k0h;
+                // resolution mode: every k_j depends on the node k_0 (dk_j/dk_0 =
+                // k_0/k_j, dk_0/dk_0 = 1) and dk_0/d ln f = (dQ/2) g_k, so
+                // d loglik/d ln f gains (dQ/2) g_k [Re kbar_0 + k_0 sum_j Re(conj(kbar_j)/k_j)]
+                const float wres = RES ? qd.y * g_hi : 0.f;
+                float res_sum = 0.f, res_k0 = 0.f;
+                auto acc_u_nonedge = [&](int idx, float re, float im) __attribute__((always_inline)) {
+                    acc_add(oUr + idx, re);
+                    acc_add(oUi + idx, im);
+                    if constexpr (RES) res_sum += re;
+                };
                 auto adj_step = [&](int j, auto TOP, auto BOT) __attribute__((always_inline)) {
                     const bool top = pos_flag(TOP, j == 0), bot = pos_flag(BOT, j == n);
                     const float4 Ij = sm.itf[j];
@@ -952,6 +969,11 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     if constexpr (T::STORE)
                         kkj = k_real ? make_float2(kj.re * kj1.re, kj.re * kj1.im) : cmul(kc(kj), kc(kj1));
                     acc_fma2(oS + j, rr.x, kkj.x, -rr.y, kkj.y);
+                    if (RES && top) {
+                        // kbar_0 = conj(k_1) conj(P) rbar (the fronting has no phase)
+                        const float2 H2 = make_float2(fmaf(2.f, gg.x, sr.x), fmaf(2.f, gg.y, sr.y));
+                        res_k0 = fmaf(kj1.re, H2.x, kj1.im * H2.y);
+                    }
                     if (!top) {
                         const float2 H2 = make_float2(fmaf(2.f, gg.x, sr.x), fmaf(2.f, gg.y, sr.y)); // conj(P) rbar
                         kbar = cfmac(kc(kj1), H2, kbar);
@@ -963,6 +985,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         if (em) {
                             if (edge) {
                                 const int slot = eq_cnt + __popc(em & ((1u << lane) - 1u));
+                                if constexpr (RES) sh_eq[warp][EQF - 1][slot] = make_float2(k0h * wres, 0.f);
                                 if constexpr (T::SMEM_ACC) {
                                     sh_eq[warp][0][slot] = make_float2(k0h, k0l);
                                     sh_eq[warp][1][slot] = Zj;
@@ -987,8 +1010,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         if (!edge) {
                             const float2 kq = cmul(kbar, kc(kj));
                             const float inv = m2 > 0.f ? rcp_approx(m2) : 0.f;
-                            acc_add(oUr + j - 1, kq.x * inv);
-                            acc_add(oUi + j - 1, -kq.y * inv);
+                            acc_u_nonedge(j - 1, kq.x * inv, -kq.y * inv);
                         }
                     }
                     Xb_up = Xb_in;
@@ -999,8 +1021,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         const float2 kk = cmul(kbar, kc(kj));
                         const float m2 = fmaf(kj.re, kj.re, kj.im * kj.im);
                         const float inv = m2 > 0.f ? rcp_approx(m2) : 0.f;
-                        acc_add(oUr + j, kk.x * inv);
-                        acc_add(oUi + j, -kk.y * inv);
+                        acc_u_nonedge(j, kk.x * inv, -kk.y * inv);
                     }
                 };
                 if constexpr (T::UNROLL) {
@@ -1018,6 +1039,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     for (int j = 1; j <= n - 1; ++j) adj_step(j, Pos<kNo>{}, Pos<kNo>{});
                     adj_step(n, Pos<kRt>{}, Pos<kYes>{});
                 }
+                if constexpr (RES) gres_acc = fmaf(wres, fmaf(k0h, res_sum, res_k0), gres_acc);
             }
         }
 
@@ -1079,9 +1101,9 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 }
                 __syncthreads();
             }
-            {   // loglik (float pair), d/dscale, d/dbkg live in the kn == 0 lanes;
+            {   // per-thread loglik (float pair), d/dscale, d/dbkg, d/d ln(dQ scale):
                 // warp sums stay on the FP32 pipe, FP64 only across warps
-                float h = ll_hi, l = ll_lo, a1 = gsc_acc, a2 = gbk_acc;
+                float h = ll_hi, l = ll_lo, a1 = gsc_acc, a2 = gbk_acc, a3 = gres_acc;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     const float h2 = __shfl_xor_sync(kFull, h, o), l2 = __shfl_xor_sync(kFull, l, o);
@@ -1091,27 +1113,29 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     l = __fadd_rn(__fadd_rn(l, l2), e);
                     a1 += __shfl_xor_sync(kFull, a1, o);
                     a2 += __shfl_xor_sync(kFull, a2, o);
+                    if constexpr (RES) a3 += __shfl_xor_sync(kFull, a3, o);
                 }
                 if (lane == 0) {
                     sh_redd[warp][0] = (double)h + (double)l;
                     sh_redd[warp][1] = a1;
                     sh_redd[warp][2] = a2;
+                    sh_redd[warp][3] = a3;
                 }
             }
             __syncthreads();
-            if (tid < 3) {
+            if (tid < (RES ? 4 : 3)) {
                 double s = 0.0;
                 for (int w = 0; w < T::WARPS; ++w) s += sh_redd[w][tid];
                 sh_raw[4 * n + 3 + tid] = s;
             }
             __syncthreads();
-            const int nout = GRAD ? 4 * n + 6 : 1;
+            const int nout = GRAD ? 4 * n + (RES ? 7 : 6) : 1;
             const int off0 = GRAD ? 0 : 4 * n + 3; // loglik mode: llsum only
             if (si.n_chunks == 1) {
-                finalize_stack<MODE>(sh_raw, n, p, wi.stack, si.par_off, ka.ll_out, ka.grad_out, tid,
-                                     BLOCK);
+                finalize_stack<MODE>(sh_raw, n, p, wi.stack, si.par_off, ka.ll_out, ka.grad_out, ka.res_out,
+                                     tid, BLOCK);
             } else {
-                double *slot = ka.partials + si.part_base + (int64_t)wi.chunk * (4 * n + 6);
+                double *slot = ka.partials + si.part_base + (int64_t)wi.chunk * n_slot(n);
                 for (int i = tid; i < nout; i += BLOCK) slot[off0 + i] = sh_raw[off0 + i];
                 __threadfence();
                 __syncthreads();
@@ -1125,12 +1149,12 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     for (int i = tid; i < nout; i += BLOCK) {
                         double s = 0.0;
                         for (int c = 0; c < si.n_chunks; ++c)
-                            s += __ldcg(ka.partials + si.part_base + (int64_t)c * (4 * n + 6) + off0 + i);
+                            s += __ldcg(ka.partials + si.part_base + (int64_t)c * n_slot(n) + off0 + i);
                         sh_raw[off0 + i] = s;
                     }
                     __syncthreads();
                     finalize_stack<MODE>(sh_raw, n, p, wi.stack, si.par_off, ka.ll_out, ka.grad_out,
-                                         tid, BLOCK);
+                                         ka.res_out, tid, BLOCK);
                     if (tid == 0) ka.stack_done[wi.stack] = 0;
                 }
             }
@@ -1212,7 +1236,7 @@ cudaError_t occupancy_one(int K, int *blocks)
 
 bool mixed_bucket_ok(int mode, int nmax)
 {
-    if (mode == kGrad) {
+    if (is_grad_mode(mode)) {
 #define X(B) if (nmax == B) return true;
         NR_GRAD_BUCKETS(X)
 #undef X
@@ -1223,7 +1247,7 @@ bool mixed_bucket_ok(int mode, int nmax)
 
 int mixed_block_threads(int mode, int nmax)
 {
-    if (mode != kGrad) return nmax == 1 ? Traits<kModel, 1>::BLOCK : Traits<kModel, 0>::BLOCK;
+    if (!is_grad_mode(mode)) return nmax == 1 ? Traits<kModel, 1>::BLOCK : Traits<kModel, 0>::BLOCK;
 #define X(B) if (nmax == B) return Traits<kGrad, B>::BLOCK;
     NR_GRAD_BUCKETS(X)
 #undef X
@@ -1232,7 +1256,7 @@ int mixed_block_threads(int mode, int nmax)
 
 size_t mixed_dyn_smem(int mode, int nmax)
 {
-    if (mode != kGrad) return 0;
+    if (!is_grad_mode(mode)) return 0;
 #define X(B) if (nmax == B) return Traits<kGrad, B>::DYN;
     NR_GRAD_BUCKETS(X)
 #undef X
@@ -1246,6 +1270,11 @@ cudaError_t mixed_occupancy(int mode, int nmax, int K, int *blocks)
         return nmax == 1 ? occupancy_one<kModel, 1>(K, blocks) : occupancy_one<kModel, 0>(K, blocks);
     case kLoglik:
         return nmax == 1 ? occupancy_one<kLoglik, 1>(K, blocks) : occupancy_one<kLoglik, 0>(K, blocks);
+    case kGradRes:
+#define X(B) if (nmax == B) return occupancy_one<kGradRes, B>(K, blocks);
+        NR_GRAD_BUCKETS(X)
+#undef X
+        break;
     default:
 #define X(B) if (nmax == B) return occupancy_one<kGrad, B>(K, blocks);
         NR_GRAD_BUCKETS(X)
@@ -1264,6 +1293,11 @@ cudaError_t launch_mixed(int mode, int nmax, int grid, const KernelArgs &a, cons
     case kLoglik:
         return nmax == 1 ? launch_one<kLoglik, 1>(grid, K, a, qc, st)
                          : launch_one<kLoglik, 0>(grid, K, a, qc, st);
+    case kGradRes:
+#define X(B) if (nmax == B) return launch_one<kGradRes, B>(grid, K, a, qc, st);
+        NR_GRAD_BUCKETS(X)
+#undef X
+        break;
     default:
 #define X(B) if (nmax == B) return launch_one<kGrad, B>(grid, K, a, qc, st);
         NR_GRAD_BUCKETS(X)

@@ -363,3 +363,53 @@ def test_plan_before_capture_and_graph_replay():
         graph.replay()
     torch.cuda.synchronize()
     assert torch.equal(ll, ref_ll) and torch.equal(g, ref_g)
+
+
+# ---------------------------------------------- resolution-scale derivative
+def res_err(wl, g, gr, g_ref, gr_ref):
+    """The resolution derivative as one more gradient component (typical
+    scale 1, like the model scale): max over stacks of the scaled error over
+    the stack's largest scaled component."""
+    po = wl.par_off
+    worst = 0.0
+    for s in range(wl.n_stacks):
+        typ = W.typical_scale(int(wl.n_layers[s]))
+        ref = np.append(g_ref[po[s]:po[s + 1]] * typ, gr_ref[s])
+        got = np.append(g[po[s]:po[s + 1]] * typ, gr[s])
+        worst = max(worst, float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+    return worst
+
+
+@pytest.mark.parametrize("name,S,kw", [("thick_oxide", 48, {}), ("film_1l", 40, {}), ("oled_cofit", 4, {}),
+                                       ("uneven", 24, {}), ("vi_step", 2, {}),
+                                       ("oled_cofit", 3, {"chunk_q": 40, "tile_q": 3})])
+def test_resolution_derivative_parity(name, S, kw):
+    wl = W.make_workload(name, n_stacks=S)
+    ctx = nr.Context(n_quad=wl.n_quad, **kw)
+    b = nr.Batch.from_workload(wl)
+    ll, g, gr = (t.cpu().numpy() for t in ctx.loglik_grad_res(b))
+    ll0, g0 = (t.cpu().numpy() for t in ctx.loglik_grad(b))
+    assert ctx.device_status() == 0
+    ctx.close()
+    ref_ll, ref_g, ref_r = oracle.batch("grad_res", wl.n_layers, wl.params, wl.dataset, wl.q_off, wl.q, wl.dq,
+                                        wl.r_obs, wl.r_err, wl.n_quad)
+    assert np.all(np.isfinite(gr))
+    assert np.max(np.abs(ll - ref_ll) / np.abs(ref_ll)) <= TOL_LL
+    assert res_err(wl, g, gr, ref_g, ref_r) <= TOL_G
+    # the log-likelihood and parameter gradient are those of nr_loglik_grad
+    assert np.max(np.abs(ll - ll0) / np.abs(ll0)) <= 1e-6
+    assert grad_err(wl, g, g0) <= 1e-5
+
+
+def test_resolution_derivative_host_batch_and_fp64_refusal():
+    wl = W.make_workload("thick_oxide", n_stacks=6)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    lld, gd, rd = ctx.loglik_grad_res(nr.Batch.from_workload(wl))
+    llh, gh, rh = ctx.loglik_grad_res(nr.Batch.from_workload(wl, device="cpu", pin=True))
+    assert not rh.is_cuda
+    assert torch.equal(rd.cpu(), rh) and torch.equal(gd.cpu(), gh)
+    ctx.close()
+    ctx64 = nr.Context(n_quad=wl.n_quad, precision="fp64")
+    with pytest.raises(nr.NRError):
+        ctx64.loglik_grad_res(nr.Batch.from_workload(wl))
+    ctx64.close()
