@@ -62,6 +62,7 @@ def _lib(precision: str = "double") -> ctypes.CDLL:
             lib.oracle_model.argtypes = [c_int, D, c_int, D, D, c_int, c_int, D]
             lib.oracle_loglik_grad.argtypes = [c_int, D, c_int, D, D, D, D, c_int, D, D]
             lib.oracle_loglik_grad_res.argtypes = [c_int, D, c_int, D, D, D, D, c_int, D]
+            lib.oracle_sld_profile.argtypes = [c_int, D, c_int, D, D, D]
             lib.oracle_batch.argtypes = [c_int, c_int, I32, D, I32, c_int, I64, D, D, D, D,
                                          c_int, c_int, D, D, D]
             _LIBS[precision] = lib
@@ -142,6 +143,16 @@ def loglik_grad_res(n: int, params, Q, dQ, Robs, err, K: int, precision: str = "
     _check(_lib(precision).oracle_loglik_grad_res(n, _d(p), Q.size, _d(Q), _d(dQ), _d(Robs), _d(err), K,
                                                   _d(out)), "loglik_grad_res")
     return float(out[0])
+
+
+def sld_profile(n: int, params, z, precision: str = "double"):
+    """(rho(z), iota(z)) of one stack: interface steps smoothed by the
+    Gaussian roughness (error-function profile), depth z in A from the
+    fronting/first-layer interface."""
+    p, z = _f64(params), _f64(z)
+    rho, iota = np.zeros(z.size), np.zeros(z.size)
+    _check(_lib(precision).oracle_sld_profile(n, _d(p), z.size, _d(z), _d(rho), _d(iota)), "sld_profile")
+    return rho, iota
 
 
 def batch(mode: str, n_layers, params, dataset, q_off, Q, dQ, Robs, err, K: int,

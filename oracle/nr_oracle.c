@@ -32,7 +32,13 @@
  *    f of every dQ_i (dQ_i -> f dQ_i, derivative in ln f at f = 1): the
  *    quantity a fit of a shared smearing percentage needs (Sec. 4.2, the
  *    LED fit's smearing parameter); one more dual pass, seeded on the node
- *    positions, dq_k / d ln f = sqrt(2) sigma_Q x_k.
+ *    positions, dq_k / d ln f = sqrt(2) sigma_Q x_k;
+ *  - the SLD profile of a stack through its depth z, the curve drawn with
+ *    posterior bands in the paper's figures (Sec. 4.1 quartz, Sec. 4.2 LED):
+ *    rho(z) = rho_0 + sum_j (rho_{j+1} - rho_j) (1 + erf((z - z_j) /
+ *    (sqrt(2) sigma_j))) / 2, interface j at depth z_j = d_1 + ... + d_j
+ *    (z_0 = 0), each step smoothed by the Gaussian roughness of that
+ *    interface; the same for the absorption iota(z).
  *
  * Readings where the paper is silent (the paper prints no reflectivity
  * equation):
@@ -69,6 +75,7 @@ typedef long double _Complex cplx;
 #define R_LOG logl
 #define R_FABS fabsl
 #define R_CBRT cbrtl
+#define R_ERF erfl
 #define C_SQRT csqrtl
 #define C_EXP cexpl
 #define C_RE creall
@@ -83,6 +90,7 @@ typedef double _Complex cplx;
 #define R_LOG log
 #define R_FABS fabs
 #define R_CBRT cbrt
+#define R_ERF erf
 #define C_SQRT csqrt
 #define C_EXP cexp
 #define C_RE creal
@@ -464,6 +472,30 @@ int oracle_loglik_grad_res(int n, const double *params, int nq, const double *Q,
     int st = loglik_dual(&s, nq, Q, dQ, Robs, err, &qd, 1, &v);
     if (st) return st;
     *gres = (double)C_RE(v.t);
+    return OR_OK;
+}
+
+/* SLD and absorption profiles of one stack at nz depths z (A); either output
+ * may be NULL.  sigma_j = 0 gives the sharp step (value of the deeper medium
+ * at z = z_j itself, the erf's sign convention at 0). */
+int oracle_sld_profile(int n, const double *params, int nz, const double *z, double *rho, double *iota)
+{
+    if (check_stack(n, params)) return OR_EINVAL;
+    const double *d = params, *r = params + n, *io = params + 2 * n + 2, *sg = params + 3 * n + 3;
+    for (int i = 0; i < nz; ++i) {
+        real zr = (real)z[i], depth = 0, vr = (real)r[0], vi = 0;
+        for (int j = 0; j <= n; ++j) {
+            if (j >= 1) depth += (real)d[j - 1];
+            real step;
+            if (sg[j] > 0) step = (1 + R_ERF((zr - depth) / (R_SQRT((real)2) * (real)sg[j]))) / 2;
+            else step = zr >= depth ? 1 : 0;
+            real io_j = j >= 1 ? (real)io[j - 1] : 0, io_j1 = (real)io[j];
+            vr += ((real)r[j + 1] - (real)r[j]) * step;
+            vi += (io_j1 - io_j) * step;
+        }
+        if (rho) rho[i] = (double)vr;
+        if (iota) iota[i] = (double)vi;
+    }
     return OR_OK;
 }
 

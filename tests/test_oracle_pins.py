@@ -9,6 +9,7 @@ import math
 
 import numpy as np
 import pytest
+import scipy.signal
 import scipy.stats
 
 import oracle
@@ -384,3 +385,53 @@ def test_batch_resolution_mode_matches_single_stack_calls():
     for s in range(wl.n_stacks):
         Q, dQ, Ro, e = wl.dataset_arrays(int(wl.dataset[s]))
         assert gr[s] == oracle.loglik_grad_res(int(wl.n_layers[s]), wl.stack_params(s), Q, dQ, Ro, e, wl.n_quad)
+
+
+# -------------------------------------------------------------- SLD profile
+def test_sld_profile_sharp_steps_and_far_field():
+    """sigma = 0: the profile is the media's SLDs between the interface
+    depths; far outside it is the fronting and backing value."""
+    d = [120.0, 35.0, 260.0]
+    rho = [0.0, 4.1e-6, -0.4e-6, 2.9e-6, 2.07e-6]
+    iota = [1e-8, 0.0, 3e-8, 0.0]
+    p = W.pack(d, rho, iota, [0.0] * 4, 1.0, 0.0)
+    edges = np.concatenate([[0.0], np.cumsum(d)])
+    z = np.linspace(-50, 480, 531)
+    r, i = oracle.sld_profile(3, p, z)
+    medium = np.searchsorted(edges, z, side="right")   # 0 fronting .. 4 backing
+    # the profile is rho_0 plus the steps: exact up to the rounding of that sum
+    np.testing.assert_allclose(r, np.asarray(rho)[medium], rtol=0, atol=1e-20)
+    np.testing.assert_allclose(i, np.concatenate([[0.0], iota])[medium], rtol=0, atol=1e-22)
+    p2 = W.pack(d, rho, iota, [4.0, 9.0, 3.0, 6.0], 1.0, 0.0)
+    r2, _ = oracle.sld_profile(3, p2, np.array([-400.0, 1200.0]))
+    assert abs(r2[0] - rho[0]) < 1e-20 and abs(r2[1] - rho[-1]) < 1e-20
+
+
+def test_sld_profile_single_interface_midpoint():
+    p = W.pack([], [1.5e-6, 6.3e-6], [0.0], [7.0], 1.0, 0.0)
+    r, _ = oracle.sld_profile(0, p, np.array([0.0, -7.0, 7.0]))
+    assert abs(r[0] - (1.5e-6 + 6.3e-6) / 2) < 1e-21
+    assert abs((r[1] - 1.5e-6) + (r[2] - 6.3e-6)) < 1e-21       # odd about the interface
+
+
+def test_sld_profile_is_gaussian_smoothed_step_profile():
+    """With one roughness on every interface the profile is the sharp profile
+    convolved with a normal density of that width (brute-force sum on a fine
+    grid), whatever the layer spacing."""
+    d = [30.0, 8.0, 55.0]
+    rho = [0.0, 5.2e-6, 1.1e-6, 3.4e-6, 2.07e-6]
+    sig = 6.0
+    sharp = W.pack(d, rho, [0.0] * 4, [0.0] * 4, 1.0, 0.0)
+    rough = W.pack(d, rho, [0.0] * 4, [sig] * 4, 1.0, 0.0)
+    h = 0.01
+    # cell-centred samples: no sample sits on an interface depth
+    zf = -150 + h * (np.arange(40000) + 0.5)
+    step, _ = oracle.sld_profile(3, sharp, zf)
+    t = h * np.arange(-6000, 6001)
+    kern = np.exp(-0.5 * (t / sig) ** 2)
+    kern /= kern.sum()
+    conv = scipy.signal.fftconvolve(step, kern, mode="same")
+    z = np.arange(-40.0, 130.0, 1.7)
+    idx = np.round((z - zf[0]) / h).astype(int)
+    r, _ = oracle.sld_profile(3, rough, zf[idx])
+    np.testing.assert_allclose(r, conv[idx], rtol=0, atol=1e-6 * max(abs(x) for x in rho))
