@@ -165,6 +165,25 @@ nr_status nr_loglik_grad(nr_ctx *ctx, const nr_batch *batch, double *loglik, dou
 nr_status nr_loglik_grad_res(nr_ctx *ctx, const nr_batch *batch, double *loglik, double *grad,
                              double *grad_res, void *stream);
 
+/* SLD and absorption depth profiles of every stack, the curves the paper's
+ * figures draw with posterior bands (Sec. 4.1 quartz film, Sec. 4.2 LED):
+ *   rho(z) = rho_0 + sum_{j=0..n} (rho_{j+1} - rho_j) (1 + erf((z - z_j) / (sqrt(2) sigma_j))) / 2
+ * with z_j = d_1 + ... + d_j the depth of interface j below the fronting
+ * (z_0 = 0), and iota(z) alike (iota_0 = 0); sigma_j = 0 is a sharp step
+ * that takes the deeper medium's value at z = z_j.
+ *   batch:    only n_stacks, n_layers (HOST), params and memory are read;
+ *             datasets may be absent.
+ *   z, nz:    depths in A (same memory kind as the batch), shared by all stacks.
+ *   rho_out, iota_out: [n_stacks * nz] floats, stack-major (either may be
+ *             NULL, not both).
+ * Device batches run asynchronously on `stream`; host batches are staged
+ * and synchronised.  The call uploads the stacks' parameter offsets into a
+ * context buffer: calls of one context must not overlap on different
+ * streams.  Non-finite parameters (or sigma < 0) raise
+ * NR_FLAG_NONFINITE_PARAM.  Errors: NR_EINVAL, NR_ECUDA. */
+nr_status nr_sld_profile(nr_ctx *ctx, const nr_batch *batch, const float *z, int32_t nz, float *rho_out,
+                         float *iota_out, void *stream);
+
 /* Synchronise `stream`, return the sticky device flags raised since the
  * last call (NR_FLAG_*) in *flags and clear them.  Returns NR_ENONFINITE
  * when any flag was set, NR_OK otherwise. */

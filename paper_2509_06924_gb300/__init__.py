@@ -33,8 +33,8 @@ NR_FLAG_NONFINITE_PARAM, NR_FLAG_BAD_Q, NR_FLAG_BAD_ERR = 1, 2, 4
 MAX_LAYERS = 64
 MAX_QUAD = 32
 EXPORTS = ("nr_create", "nr_destroy", "nr_last_error", "nr_plan", "nr_reflectivity", "nr_loglik",
-           "nr_loglik_grad", "nr_loglik_grad_res", "nr_device_status", "nr_quadrature", "nr_plan_info",
-           "nr_loglik_grad_noalloc")
+           "nr_loglik_grad", "nr_loglik_grad_res", "nr_sld_profile", "nr_device_status", "nr_quadrature",
+           "nr_plan_info", "nr_loglik_grad_noalloc")
 NOALLOC_MAX_STACKS = 16384
 
 
@@ -284,6 +284,20 @@ class Context:
                                             ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(r.data_ptr()),
                                             _stream_handle(stream)))
         return ll, g, r
+
+    def sld_profile(self, batch: Batch, z, rho_out=None, iota_out=None, stream=None):
+        """(rho(z), iota(z)) of every stack, float32 [S, nz]: error-function
+        interfaces of width sigma_j at depths z_j = d_1 + ... + d_j.  z: a
+        float32 tensor in the batch's memory kind."""
+        import torch
+        nz = int(z.numel())
+        rho = self._alloc(batch, batch.n_stacks * nz, torch.float32, rho_out)
+        iota = self._alloc(batch, batch.n_stacks * nz, torch.float32, iota_out)
+        cb = batch._c()
+        _check(self._lib.nr_sld_profile(self._h, ctypes.byref(cb), ctypes.c_void_p(z.data_ptr()), nz,
+                                        ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(iota.data_ptr()),
+                                        _stream_handle(stream)))
+        return rho.view(batch.n_stacks, nz), iota.view(batch.n_stacks, nz)
 
     def device_status(self, stream=None) -> int:
         """Synchronise and return (and clear) the sticky NR_FLAG_* word."""

@@ -200,6 +200,7 @@ struct nr_ctx {
     uint64_t clock = 0;
     // host-memory staging
     DevBuf s_params, s_q, s_dq, s_robs, s_rerr, s_out, s_ll, s_grad, s_res;
+    DevBuf p_off, p_nl, p_z, p_rho, p_iota; // SLD-profile metadata and host-call staging
 };
 
 namespace {
@@ -651,6 +652,59 @@ nr_status nr_loglik_grad_res(nr_ctx *ctx, const nr_batch *batch, double *loglik,
                              void *stream)
 {
     return compute(ctx, batch, kGradRes, nullptr, loglik, grad, grad_res, stream);
+}
+
+nr_status nr_sld_profile(nr_ctx *ctx, const nr_batch *batch, const float *z, int32_t nz, float *rho_out,
+                         float *iota_out, void *stream)
+{
+    if (!ctx) return fail(NR_EINVAL, "context is NULL");
+    if (!batch) return fail(NR_EINVAL, "batch is NULL");
+    const nr_batch *b = batch;
+    if (b->n_stacks < 0) return fail(NR_EINVAL, "n_stacks < 0");
+    if (b->memory != NR_MEM_DEVICE && b->memory != NR_MEM_HOST) return fail(NR_EINVAL, "bad memory kind");
+    if (nz < 0) return fail(NR_EINVAL, "nz < 0");
+    const int S = b->n_stacks;
+    if (S == 0 || nz == 0) return NR_OK;
+    if (!b->n_layers || !b->params) return fail(NR_EINVAL, "n_layers/params pointer is NULL");
+    if (!z) return fail(NR_EINVAL, "z is NULL");
+    if (!rho_out && !iota_out) return fail(NR_EINVAL, "rho_out and iota_out are both NULL");
+    std::vector<int64_t> off(S);
+    int64_t np = 0;
+    for (int s = 0; s < S; ++s) {
+        if (b->n_layers[s] < 0 || b->n_layers[s] > NR_MAX_LAYERS)
+            return fail(NR_EINVAL, "stack %d: n_layers %d outside [0, %d]", s, b->n_layers[s], NR_MAX_LAYERS);
+        off[s] = np;
+        np += 4 * (int64_t)b->n_layers[s] + 6;
+    }
+    NR_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    NR_CUDA(ctx->p_off.ensure(sizeof(int64_t) * S));
+    NR_CUDA(ctx->p_nl.ensure(sizeof(int32_t) * S));
+    NR_CUDA(cudaMemcpyAsync(ctx->p_off.p, off.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, st));
+    NR_CUDA(cudaMemcpyAsync(ctx->p_nl.p, b->n_layers, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st));
+    const size_t nout = sizeof(float) * (size_t)S * nz;
+    const double *d_par = b->params;
+    const float *d_z = z;
+    float *d_rho = rho_out, *d_iota = iota_out;
+    if (b->memory == NR_MEM_HOST) {
+        NR_CUDA(ctx->s_params.ensure(sizeof(double) * np));
+        NR_CUDA(ctx->p_z.ensure(sizeof(float) * nz));
+        NR_CUDA(cudaMemcpyAsync(ctx->s_params.p, b->params, sizeof(double) * np, cudaMemcpyHostToDevice, st));
+        NR_CUDA(cudaMemcpyAsync(ctx->p_z.p, z, sizeof(float) * nz, cudaMemcpyHostToDevice, st));
+        d_par = ctx->s_params.as<double>();
+        d_z = ctx->p_z.as<float>();
+        if (rho_out) { NR_CUDA(ctx->p_rho.ensure(nout)); d_rho = ctx->p_rho.as<float>(); }
+        if (iota_out) { NR_CUDA(ctx->p_iota.ensure(nout)); d_iota = ctx->p_iota.as<float>(); }
+    }
+    cudaError_t e = launch_profile(d_par, ctx->p_off.as<int64_t>(), ctx->p_nl.as<int32_t>(), S, d_z, nz, d_rho,
+                                   d_iota, ctx->d_status, ctx->sms, st);
+    if (e != cudaSuccess) return fail(NR_ECUDA, "profile launch: %s", cudaGetErrorString(e));
+    if (b->memory == NR_MEM_HOST) {
+        if (rho_out) NR_CUDA(cudaMemcpyAsync(rho_out, d_rho, nout, cudaMemcpyDeviceToHost, st));
+        if (iota_out) NR_CUDA(cudaMemcpyAsync(iota_out, d_iota, nout, cudaMemcpyDeviceToHost, st));
+        NR_CUDA(cudaStreamSynchronize(st));
+    }
+    return NR_OK;
 }
 
 nr_status nr_device_status(nr_ctx *ctx, void *stream, int32_t *flags)

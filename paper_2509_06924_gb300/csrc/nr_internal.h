@@ -91,6 +91,11 @@ constexpr int kFp64Block = 128;
 cudaError_t launch_fp64(int mode, const KernelArgs &a, const QuadConst &qc, cudaStream_t st);
 cudaError_t launch_fp64_finalize(int mode, int n_stacks, const KernelArgs &a, cudaStream_t st);
 
+// ---- SLD profiles (nr_profile.cu) ----
+cudaError_t launch_profile(const double *params, const int64_t *par_off, const int32_t *n_layers, int n_stacks,
+                           const float *z, int nz, float *rho_out, float *iota_out, int32_t *status, int sms,
+                           cudaStream_t st);
+
 // Raw per-stack sums of the mixed gradient kernels, and the stride of a
 // chunk's partial-sum slot: [accD (n) | accUr (n+1) | accUi (n+1) |
 // accS (n+1) | llsum | gscale | gbkg | gres].

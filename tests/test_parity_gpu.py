@@ -413,3 +413,57 @@ def test_resolution_derivative_host_batch_and_fp64_refusal():
     with pytest.raises(nr.NRError):
         ctx64.loglik_grad_res(nr.Batch.from_workload(wl))
     ctx64.close()
+
+
+# ------------------------------------------------------------- SLD profiles
+def profile_ref(wl, z):
+    po = wl.par_off
+    rho = np.zeros((wl.n_stacks, z.size))
+    iota = np.zeros((wl.n_stacks, z.size))
+    for s in range(wl.n_stacks):
+        rho[s], iota[s] = oracle.sld_profile(int(wl.n_layers[s]), wl.params[po[s]:po[s + 1]], z.astype(np.float64))
+    return rho, iota
+
+
+@pytest.mark.parametrize("name,S", [("thick_oxide", 16), ("oled_cofit", 9), ("uneven", 40), ("vi_step", 6)])
+def test_sld_profile_parity(name, S):
+    wl = W.make_workload(name, n_stacks=S)
+    depth = max(float(np.sum(wl.stack_params(s)[:int(wl.n_layers[s])])) for s in range(S))
+    z = np.linspace(-60.0, depth + 60.0, 1037).astype(np.float32)   # ragged against the 256-thread sweep
+    ctx = nr.Context(n_quad=wl.n_quad)
+    b = nr.Batch.from_workload(wl)
+    rho, iota = ctx.sld_profile(b, torch.as_tensor(z, device="cuda"))
+    assert ctx.device_status() == 0
+    rho, iota = rho.cpu().numpy(), iota.cpu().numpy()
+    ref_r, ref_i = profile_ref(wl, z)
+    for s in range(S):
+        scale_r = np.max(np.abs(ref_r[s]))
+        scale_i = max(np.max(np.abs(ref_i[s])), 1e-12)
+        assert np.max(np.abs(rho[s] - ref_r[s])) <= 2e-6 * scale_r
+        assert np.max(np.abs(iota[s] - ref_i[s])) <= 2e-6 * scale_i
+    ctx.close()
+
+
+def test_sld_profile_sharp_steps_host_batch_and_flags():
+    d = [120.0, 35.0]
+    rho = [0.0, 4.1e-6, -0.4e-6, 2.07e-6]
+    stacks = [(2, W.pack(d, rho, [1e-8, 0.0, 0.0], [0.0, 0.0, 0.0], 1.0, 0.0), 0),
+              (0, W.pack([], [0.0, 2.07e-6], [0.0], [3.0], 1.0, 0.0), 0)]
+    q = W.log_grid(10, 0.01, 0.2)
+    wl = custom_workload(stacks, [(q, 0.05 * q.astype(np.float64))])
+    z = np.array([-10.0, 0.0, 119.0, 120.0, 154.0, 155.0, 400.0], np.float32)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    rho_d, iota_d = ctx.sld_profile(nr.Batch.from_workload(wl), torch.as_tensor(z, device="cuda"))
+    rho_h, iota_h = ctx.sld_profile(nr.Batch.from_workload(wl, device="cpu", pin=True), torch.as_tensor(z))
+    assert torch.equal(rho_d.cpu(), rho_h) and torch.equal(iota_d.cpu(), iota_h)
+    # sharp steps: the deeper medium's value from the interface depth on
+    np.testing.assert_allclose(rho_h[0].numpy(), [0.0, 4.1e-6, 4.1e-6, -0.4e-6, -0.4e-6, 2.07e-6, 2.07e-6],
+                               rtol=0, atol=2e-12)
+    assert abs(float(rho_h[1, 1]) - 2.07e-6 / 2) < 1e-12
+    assert ctx.device_status() == 0
+    bad = wl.params.copy()
+    bad[0] = np.nan
+    wl_bad = custom_workload([(2, bad[:14], 0)], [(q, 0.05 * q.astype(np.float64))], data_from_oracle=False)
+    ctx.sld_profile(nr.Batch.from_workload(wl_bad), torch.as_tensor(z, device="cuda"))
+    assert ctx.device_status() & nr.NR_FLAG_NONFINITE_PARAM
+    ctx.close()
