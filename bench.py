@@ -264,6 +264,65 @@ def run_reference(args):
     return 0
 
 
+def hmc_measure(nr, W, dev, chains=1024, n_leapfrog=10, eps=5e-4, steps=5, warm=2) -> dict:
+    """One on-device HMC transition of `chains` chains of the 12-layer,
+    3-contrast co-fit (the VI/HMC-step configuration with 1024 chains and 10
+    leapfrog steps), captured as a CUDA graph and replayed; fresh normal and
+    uniform draws are written before each replay.  Evaluations per step:
+    chains x 3 contrasts x 300 Q x 21 nodes x (L + 1)."""
+    import torch
+    nl, ds, src, val, lo, hi, ut = W.cofit_sampler_model("vi_step")
+    wl = W.make_workload("vi_step", n_stacks=1)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    q, dq, ro, re = (torch.as_tensor(a, device=dev) for a in (wl.q, wl.dq, wl.r_obs, wl.r_err))
+    smp = nr.Sampler(ctx, chains, nl, ds, wl.q_off, q, dq, ro, re, src, val, lo, hi)
+    P = ut.size
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.SEED_BASE + 5)
+    u = torch.as_tensor(ut, device=dev)[None, :] + 0.02 * torch.randn(chains, P, generator=gen, device=dev,
+                                                                       dtype=torch.float64)
+    z = torch.empty(chains, P, dtype=torch.float64, device=dev)
+    lu = torch.empty(chains, dtype=torch.float64, device=dev)
+    invm = torch.ones(P, dtype=torch.float64, device=dev)
+    lp = torch.empty(chains, dtype=torch.float64, device=dev)
+    acc = torch.empty(chains, dtype=torch.int32, device=dev)
+    s = torch.cuda.Stream(device=dev)
+
+    def draws():
+        z.normal_(generator=gen)
+        lu.uniform_(generator=gen).log_()
+    n_acc = torch.zeros((), dtype=torch.int64, device=dev)
+    with torch.cuda.stream(s):
+        for _ in range(warm):               # every op of the timed loop runs (and loads) here first
+            draws()
+            smp.hmc_step(u, z, lu, invm, eps, n_leapfrog, lp, acc, stream=s)
+            n_acc += acc.sum()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        smp.hmc_step(u, z, lu, invm, eps, n_leapfrog, lp, acc, stream=s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_acc.zero_()
+    with torch.cuda.stream(s):
+        e0.record(s)
+        for _ in range(steps):
+            draws()
+            graph.replay()
+            n_acc += acc.sum()
+        e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    status = ctx.device_status()
+    evals = chains * int(wl.q_off[-1]) * wl.n_quad * (n_leapfrog + 1)
+    out = {"chains": chains, "contrasts": 3, "layers": int(nl[0]), "free_params": int(P),
+           "leapfrog_steps": n_leapfrog, "step_size": eps, "ms_per_transition": ms,
+           "evals_per_s": evals / (ms * 1e-3), "accept_rate": float(n_acc.item()) / (steps * chains),
+           "graph": True, "launches_per_transition": 3 * (n_leapfrog + 1), "device_flags": status}
+    smp.close()
+    ctx.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -378,6 +437,8 @@ def run_ours(args):
         line["fp32_issue"] = {"inst_per_eval": ipe, "achieved": value / ws * ipe / 1e12, "peak": peak_inst,
                               "unit": "T inst/s", "frac": value / ws * ipe / 1e12 / peak_inst,
                               "basis": "FP32 FFMA/FADD/FMUL per evaluation counted by ncu"}
+    if ws == 1 and not args.no_hmc:
+        line["hmc"] = hmc_measure(nr, W, dev)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line), flush=True)
@@ -395,6 +456,7 @@ def main():
     ap.add_argument("--workload", default="thick_oxide")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement (profiling runs)")
+    ap.add_argument("--no-hmc", action="store_true", help="skip the on-device HMC transition (profiling runs)")
     ap.add_argument("--stacks", type=int, default=None,
                     help="override the stack count (small profiling cases; not a bench line)")
     args = ap.parse_args()

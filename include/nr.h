@@ -233,6 +233,72 @@ nr_status nr_plan_info(nr_ctx *ctx, const nr_batch *batch, int64_t *evals, int32
 nr_status nr_loglik_grad_noalloc(const nr_batch *batch, int32_t n_quad, double *loglik, double *grad,
                                  int32_t *device_flags, void *stream);
 
+/* ------------------------------------------------------------------------
+ * On-device Hamiltonian Monte Carlo over many chains of a co-fitted model
+ * (Sec. 2.3: leapfrog integration, Eq. 7, of L steps of size dt with a
+ * diagonal mass matrix, then the Metropolis-Hastings acceptance of Eq. 8).
+ *
+ * Model of one chain: P free parameters theta_k with uniform priors on
+ * [lo_k, hi_k] (the priors of Tables 1-4), sampled in unconstrained
+ * coordinates u (Sec. 2.3.1's advice for bounded parameters):
+ *   theta_k = lo_k + (hi_k - lo_k) / (1 + exp(-u_k)),
+ *   log pi(u) = sum_c loglik_c(theta(u)) + sum_k [log s_k + log(1 - s_k)],
+ * s_k the sigmoid of u_k (prior density times Jacobian).  Each of the
+ * chain's n_contrasts contrasts is one stack whose packed slots (layout as
+ * nr_batch.params) either copy a free parameter (slot_src = k, tied across
+ * contrasts, e.g. a co-fitted substrate SLD or shared layers) or hold the
+ * fixed value slot_val.  Contrast c is fitted to dataset[c].
+ * ---------------------------------------------------------------------- */
+typedef struct nr_cofit_model {
+    int32_t n_chains;         /* C >= 1                                         */
+    int32_t n_contrasts;      /* stacks per chain, >= 1                         */
+    int32_t n_free;           /* P >= 1 free parameters per chain               */
+    const int32_t *n_layers;  /* [n_contrasts] HOST                             */
+    const int32_t *dataset;   /* [n_contrasts] HOST, into the datasets below    */
+    int32_t n_datasets;
+    const int64_t *q_off;     /* [n_datasets + 1] HOST, as nr_batch             */
+    const float *q, *dq;      /* DEVICE, as nr_batch                            */
+    const float *r_obs, *r_err;
+    const int32_t *slot_src;  /* [sum_c (4 n_c + 6)] HOST: k in [0, P) or -1    */
+    const double *slot_val;   /* [same] HOST: value of the fixed slots          */
+    const double *lo, *hi;    /* [P] HOST: prior bounds, finite, lo < hi        */
+} nr_cofit_model;
+
+typedef struct nr_sampler nr_sampler;
+
+/* Build a sampler for the model on the context's device: copies the slot
+ * tables and bounds, allocates the per-chain workspaces and plans the
+ * likelihood batch of C x n_contrasts stacks (chain-major).  The data
+ * arrays are referenced, not copied: they must outlive the sampler.
+ * Errors: NR_EINVAL (bad model), NR_ENOMEM, NR_ECUDA. */
+nr_status nr_sampler_create(nr_ctx *ctx, const nr_cofit_model *model, nr_sampler **out);
+
+/* Release the sampler (synchronises the device).  A sampler computes in its
+ * context: destroy samplers before the context. */
+void nr_sampler_destroy(nr_sampler *sampler);
+
+/* log pi(u) [C] and its gradient d log pi / du [C x P] (either may be NULL)
+ * at u [C x P]; all DEVICE, asynchronous on `stream`. */
+nr_status nr_sampler_logp_grad(nr_sampler *sampler, const double *u, double *logp, double *grad,
+                               void *stream);
+
+/* One HMC transition of every chain.
+ *   u:        [C x P] DEVICE, the chains' states; replaced by the accepted
+ *             end points (rejected chains keep theirs).
+ *   z:        [C x P] DEVICE standard-normal draws; the momentum is
+ *             p = z / sqrt(inv_mass).
+ *   log_unif: [C] DEVICE logs of uniform draws; a chain accepts iff
+ *             log_unif < H(start) - H(end) (Eq. 8; NaN rejects).
+ *   inv_mass: [P] DEVICE diagonal of M^-1.  eps: step dt; n_leapfrog: L >= 1.
+ *   logp:     [C] DEVICE log pi of the resulting states (may be NULL).
+ *   accepted: [C] DEVICE 1 / 0 (may be NULL).
+ * L + 1 likelihood-gradient evaluations of the C x n_contrasts batch; no
+ * allocation and no host synchronisation once the sampler exists, so a
+ * step can be captured in a CUDA graph.  Errors: NR_EINVAL, NR_ECUDA. */
+nr_status nr_hmc_step(nr_sampler *sampler, double *u, const double *z, const double *log_unif,
+                      const double *inv_mass, double eps, int32_t n_leapfrog, double *logp, int32_t *accepted,
+                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

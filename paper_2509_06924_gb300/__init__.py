@@ -34,7 +34,8 @@ MAX_LAYERS = 64
 MAX_QUAD = 32
 EXPORTS = ("nr_create", "nr_destroy", "nr_last_error", "nr_plan", "nr_reflectivity", "nr_loglik",
            "nr_loglik_grad", "nr_loglik_grad_res", "nr_sld_profile", "nr_device_status", "nr_quadrature",
-           "nr_plan_info", "nr_loglik_grad_noalloc")
+           "nr_plan_info", "nr_loglik_grad_noalloc", "nr_sampler_create", "nr_sampler_destroy",
+           "nr_sampler_logp_grad", "nr_hmc_step")
 NOALLOC_MAX_STACKS = 16384
 
 
@@ -57,6 +58,14 @@ class CBatch(ctypes.Structure):
                 ("memory", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("params", ctypes.c_void_p), ("q", ctypes.c_void_p), ("dq", ctypes.c_void_p),
                 ("r_obs", ctypes.c_void_p), ("r_err", ctypes.c_void_p)]
+
+
+class CCofitModel(ctypes.Structure):
+    _fields_ = [("n_chains", ctypes.c_int32), ("n_contrasts", ctypes.c_int32), ("n_free", ctypes.c_int32),
+                ("n_layers", ctypes.c_void_p), ("dataset", ctypes.c_void_p), ("n_datasets", ctypes.c_int32),
+                ("q_off", ctypes.c_void_p), ("q", ctypes.c_void_p), ("dq", ctypes.c_void_p),
+                ("r_obs", ctypes.c_void_p), ("r_err", ctypes.c_void_p), ("slot_src", ctypes.c_void_p),
+                ("slot_val", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -94,8 +103,15 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             lib.nr_quadrature.argtypes = [i32, dp, dp]
             lib.nr_plan_info.argtypes = [vp, ctypes.POINTER(CBatch), i64p, i32p, i32p, i32p, i32p]
             lib.nr_loglik_grad_noalloc.argtypes = [ctypes.POINTER(CBatch), i32, vp, vp, vp, vp]
+            lib.nr_loglik_grad_res.argtypes = [vp, ctypes.POINTER(CBatch), vp, vp, vp, vp]
+            lib.nr_sld_profile.argtypes = [vp, ctypes.POINTER(CBatch), vp, i32, vp, vp, vp]
+            lib.nr_sampler_create.argtypes = [vp, ctypes.POINTER(CCofitModel), ctypes.POINTER(vp)]
+            lib.nr_sampler_destroy.argtypes = [vp]
+            lib.nr_sampler_destroy.restype = None
+            lib.nr_sampler_logp_grad.argtypes = [vp, vp, vp, vp, vp]
+            lib.nr_hmc_step.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, i32, vp, vp, vp]
             for name in EXPORTS:
-                if name not in ("nr_destroy", "nr_last_error"):
+                if name not in ("nr_destroy", "nr_last_error", "nr_sampler_destroy"):
                     getattr(lib, name).restype = ctypes.c_int
             _LIB = lib
         return _LIB
@@ -306,6 +322,71 @@ class Context:
         if st not in (NR_OK, NR_ENONFINITE):
             _check(st)
         return int(f.value)
+
+
+class Sampler:
+    """On-device HMC over n_chains chains of a co-fitted model (nr_sampler_*,
+    nr_hmc_step).  Per contrast: n_layers, dataset (index into the datasets
+    given by q_off and the device tensors q, dq, r_obs, r_err); per packed
+    slot of the concatenated contrasts: slot_src (free parameter or -1) and
+    slot_val (fixed value); per free parameter: uniform prior bounds lo, hi.
+    States u are unconstrained: theta = lo + (hi - lo) sigmoid(u)."""
+
+    def __init__(self, ctx: Context, n_chains: int, n_layers, dataset, q_off, q, dq, r_obs, r_err, slot_src,
+                 slot_val, lo, hi):
+        import numpy as np
+        self._lib = ctx._lib
+        self._ctx = ctx                                   # the sampler lives in the context
+        self._keep = [np.ascontiguousarray(n_layers, np.int32), np.ascontiguousarray(dataset, np.int32),
+                      np.ascontiguousarray(q_off, np.int64), np.ascontiguousarray(slot_src, np.int32),
+                      np.ascontiguousarray(slot_val, np.float64), np.ascontiguousarray(lo, np.float64),
+                      np.ascontiguousarray(hi, np.float64)]
+        self._data = (q, dq, r_obs, r_err)                # referenced by the sampler
+        nl, ds, qo, src, val, lo_, hi_ = self._keep
+        self.n_chains, self.n_free = int(n_chains), int(lo_.size)
+        m = CCofitModel(self.n_chains, nl.size, self.n_free, nl.ctypes.data, ds.ctypes.data, qo.size - 1,
+                        qo.ctypes.data, q.data_ptr(), dq.data_ptr(), r_obs.data_ptr(), r_err.data_ptr(),
+                        src.ctypes.data, val.ctypes.data, lo_.ctypes.data, hi_.ctypes.data)
+        h = ctypes.c_void_p()
+        _check(self._lib.nr_sampler_create(ctx._h, ctypes.byref(m), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nr_sampler_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def logp_grad(self, u, stream=None):
+        """(log pi [C], d log pi / du [C, P]) at u [C, P] (float64, device)."""
+        import torch
+        lp = torch.empty(self.n_chains, dtype=torch.float64, device=u.device)
+        g = torch.empty_like(u)
+        _check(self._lib.nr_sampler_logp_grad(self._h, ctypes.c_void_p(u.data_ptr()),
+                                              ctypes.c_void_p(lp.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                              _stream_handle(stream)))
+        return lp, g
+
+    def hmc_step(self, u, z, log_unif, inv_mass, eps: float, n_leapfrog: int, logp_out=None, accepted_out=None,
+                 stream=None):
+        """One HMC transition of every chain, in place on u [C, P]; returns
+        (log pi [C], accepted [C] int32).  z: standard-normal draws [C, P];
+        log_unif: log of uniform draws [C]; inv_mass: [P]."""
+        import torch
+        lp = logp_out if logp_out is not None else torch.empty(self.n_chains, dtype=torch.float64,
+                                                                device=u.device)
+        acc = accepted_out if accepted_out is not None else torch.empty(self.n_chains, dtype=torch.int32,
+                                                                        device=u.device)
+        _check(self._lib.nr_hmc_step(self._h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                     ctypes.c_void_p(log_unif.data_ptr()), ctypes.c_void_p(inv_mass.data_ptr()),
+                                     float(eps), int(n_leapfrog), ctypes.c_void_p(lp.data_ptr()),
+                                     ctypes.c_void_p(acc.data_ptr()), _stream_handle(stream)))
+        return lp, acc
 
 
 def loglik_grad_noalloc(batch: Batch, n_quad: int, ll_out, grad_out, flags_out=None, stream=None) -> None:

@@ -203,6 +203,18 @@ struct nr_ctx {
     DevBuf p_off, p_nl, p_z, p_rho, p_iota; // SLD-profile metadata and host-call staging
 };
 
+// On-device HMC sampler: the replicated likelihood batch of C chains x
+// n_contrasts stacks and the per-chain workspaces (see nr_hmc.cu).
+struct nr_sampler {
+    nr_ctx *ctx = nullptr;
+    int device = 0;
+    int C = 0, P = 0, NC = 0, NS = 0;
+    std::vector<int32_t> n_layers, dataset; // [C * NC], chain-major
+    std::vector<int64_t> q_off;
+    nr_batch batch{};
+    DevBuf d_src, d_val, d_lo, d_hi, d_tie_ptr, d_tie_slot, d_params, d_ll, d_gpk, d_mom, d_u0, d_H0, d_lp0;
+};
+
 namespace {
 
 nr_status validate(const nr_batch *b)
@@ -703,6 +715,181 @@ nr_status nr_sld_profile(nr_ctx *ctx, const nr_batch *batch, const float *z, int
         if (rho_out) NR_CUDA(cudaMemcpyAsync(rho_out, d_rho, nout, cudaMemcpyDeviceToHost, st));
         if (iota_out) NR_CUDA(cudaMemcpyAsync(iota_out, d_iota, nout, cudaMemcpyDeviceToHost, st));
         NR_CUDA(cudaStreamSynchronize(st));
+    }
+    return NR_OK;
+}
+
+nr_status nr_sampler_create(nr_ctx *ctx, const nr_cofit_model *m, nr_sampler **out)
+{
+    if (!out) return fail(NR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctx || !m) return fail(NR_EINVAL, "context or model is NULL");
+    if (ctx->opt.precision != NR_MIXED) return fail(NR_EINVAL, "the samplers run on the NR_MIXED path");
+    if (m->n_chains < 1 || m->n_contrasts < 1 || m->n_free < 1) return fail(NR_EINVAL, "empty model");
+    if ((int64_t)m->n_chains * m->n_contrasts > (int64_t)1 << 30) return fail(NR_EINVAL, "model too large");
+    if (!m->n_layers || !m->dataset || !m->q_off || !m->slot_src || !m->slot_val || !m->lo || !m->hi)
+        return fail(NR_EINVAL, "model host pointer is NULL");
+    if (!m->q || !m->dq || !m->r_obs || !m->r_err) return fail(NR_EINVAL, "model data pointer is NULL");
+    const int C = m->n_chains, NC = m->n_contrasts, P = m->n_free;
+    int NS = 0;
+    for (int c = 0; c < NC; ++c) {
+        if (m->n_layers[c] < 0 || m->n_layers[c] > NR_MAX_LAYERS)
+            return fail(NR_EINVAL, "contrast %d: n_layers %d outside [0, %d]", c, m->n_layers[c], NR_MAX_LAYERS);
+        NS += 4 * m->n_layers[c] + 6;
+    }
+    for (int k = 0; k < P; ++k)
+        if (!std::isfinite(m->lo[k]) || !std::isfinite(m->hi[k]) || !(m->lo[k] < m->hi[k]))
+            return fail(NR_EINVAL, "parameter %d: bounds [%g, %g]", k, m->lo[k], m->hi[k]);
+    std::vector<int32_t> tie_ptr(P + 1, 0), tie_slot;
+    for (int i = 0; i < NS; ++i) {
+        const int k = m->slot_src[i];
+        if (k < -1 || k >= P) return fail(NR_EINVAL, "slot %d: source %d outside [-1, %d)", i, k, P);
+        if (k < 0 && !std::isfinite(m->slot_val[i])) return fail(NR_EINVAL, "slot %d: fixed value not finite", i);
+        if (k >= 0) ++tie_ptr[k + 1];
+    }
+    for (int k = 0; k < P; ++k) tie_ptr[k + 1] += tie_ptr[k];
+    tie_slot.resize(std::max(tie_ptr[P], 1));
+    {
+        std::vector<int32_t> fill(tie_ptr.begin(), tie_ptr.end() - 1);
+        for (int i = 0; i < NS; ++i)
+            if (m->slot_src[i] >= 0) tie_slot[fill[m->slot_src[i]]++] = i;
+    }
+    auto sp = std::make_unique<nr_sampler>();
+    nr_sampler &S = *sp;
+    S.ctx = ctx;
+    S.device = ctx->device;
+    S.C = C;
+    S.P = P;
+    S.NC = NC;
+    S.NS = NS;
+    S.n_layers.resize((size_t)C * NC);
+    S.dataset.resize((size_t)C * NC);
+    for (int c = 0; c < C; ++c)
+        for (int j = 0; j < NC; ++j) {
+            S.n_layers[(size_t)c * NC + j] = m->n_layers[j];
+            S.dataset[(size_t)c * NC + j] = m->dataset[j];
+        }
+    if (m->n_datasets < 1) return fail(NR_EINVAL, "n_datasets < 1");
+    S.q_off.assign(m->q_off, m->q_off + m->n_datasets + 1);
+    NR_CUDA(cudaSetDevice(ctx->device));
+    NR_CUDA(S.d_src.ensure(sizeof(int32_t) * NS));
+    NR_CUDA(S.d_val.ensure(sizeof(double) * NS));
+    NR_CUDA(S.d_lo.ensure(sizeof(double) * P));
+    NR_CUDA(S.d_hi.ensure(sizeof(double) * P));
+    NR_CUDA(S.d_tie_ptr.ensure(sizeof(int32_t) * (P + 1)));
+    NR_CUDA(S.d_tie_slot.ensure(sizeof(int32_t) * tie_slot.size()));
+    NR_CUDA(S.d_params.ensure(sizeof(double) * (size_t)C * NS));
+    NR_CUDA(S.d_ll.ensure(sizeof(double) * (size_t)C * NC));
+    NR_CUDA(S.d_gpk.ensure(sizeof(double) * (size_t)C * NS));
+    NR_CUDA(S.d_mom.ensure(sizeof(double) * (size_t)C * P));
+    NR_CUDA(S.d_u0.ensure(sizeof(double) * (size_t)C * P));
+    NR_CUDA(S.d_H0.ensure(sizeof(double) * C));
+    NR_CUDA(S.d_lp0.ensure(sizeof(double) * C));
+    NR_CUDA(cudaMemcpy(S.d_src.p, m->slot_src, sizeof(int32_t) * NS, cudaMemcpyHostToDevice));
+    NR_CUDA(cudaMemcpy(S.d_val.p, m->slot_val, sizeof(double) * NS, cudaMemcpyHostToDevice));
+    NR_CUDA(cudaMemcpy(S.d_lo.p, m->lo, sizeof(double) * P, cudaMemcpyHostToDevice));
+    NR_CUDA(cudaMemcpy(S.d_hi.p, m->hi, sizeof(double) * P, cudaMemcpyHostToDevice));
+    NR_CUDA(cudaMemcpy(S.d_tie_ptr.p, tie_ptr.data(), sizeof(int32_t) * (P + 1), cudaMemcpyHostToDevice));
+    NR_CUDA(cudaMemcpy(S.d_tie_slot.p, tie_slot.data(), sizeof(int32_t) * tie_slot.size(), cudaMemcpyHostToDevice));
+    // fixed slots in place from the start (tied ones are rewritten by every gather)
+    for (int c = 0; c < C; ++c)
+        NR_CUDA(cudaMemcpy(S.d_params.as<double>() + (size_t)c * NS, m->slot_val, sizeof(double) * NS,
+                           cudaMemcpyHostToDevice));
+    nr_batch &b = S.batch;
+    b.n_stacks = C * NC;
+    b.n_datasets = m->n_datasets;
+    b.n_layers = S.n_layers.data();
+    b.dataset = S.dataset.data();
+    b.q_off = S.q_off.data();
+    b.memory = NR_MEM_DEVICE;
+    b.params = S.d_params.as<double>();
+    b.q = m->q;
+    b.dq = m->dq;
+    b.r_obs = m->r_obs;
+    b.r_err = m->r_err;
+    Plan *pl = nullptr;
+    nr_status st = get_plan(ctx, &b, kGrad, &pl);
+    if (st != NR_OK) return st;
+    *out = sp.release();
+    return NR_OK;
+}
+
+void nr_sampler_destroy(nr_sampler *s)
+{
+    if (!s) return;
+    cudaSetDevice(s->device);
+    cudaDeviceSynchronize();
+    delete s;
+}
+
+namespace {
+CofitStageArgs stage_args(nr_sampler *S, double *u, int stage)
+{
+    CofitStageArgs a{};
+    a.C = S->C;
+    a.P = S->P;
+    a.NS = S->NS;
+    a.n_contrast = S->NC;
+    a.stage = stage;
+    a.u = u;
+    a.ll = S->d_ll.as<double>();
+    a.gpk = S->d_gpk.as<double>();
+    a.tie_ptr = S->d_tie_ptr.as<int32_t>();
+    a.tie_slot = S->d_tie_slot.as<int32_t>();
+    a.lo = S->d_lo.as<double>();
+    a.hi = S->d_hi.as<double>();
+    a.mom = S->d_mom.as<double>();
+    a.u0 = S->d_u0.as<double>();
+    a.H0 = S->d_H0.as<double>();
+    a.logp0 = S->d_lp0.as<double>();
+    return a;
+}
+
+// log-likelihood and packed gradient of every stack at the chains' u
+nr_status sampler_eval(nr_sampler *S, const double *u, cudaStream_t st)
+{
+    cudaError_t e = launch_cofit_gather(u, S->C, S->P, S->NS, S->d_src.as<int32_t>(), S->d_val.as<double>(),
+                                        S->d_lo.as<double>(), S->d_hi.as<double>(), S->d_params.as<double>(), st);
+    if (e != cudaSuccess) return fail(NR_ECUDA, "sampler gather: %s", cudaGetErrorString(e));
+    return compute(S->ctx, &S->batch, kGrad, nullptr, S->d_ll.as<double>(), S->d_gpk.as<double>(), nullptr, st);
+}
+} // namespace
+
+nr_status nr_sampler_logp_grad(nr_sampler *S, const double *u, double *logp, double *grad, void *stream)
+{
+    if (!S || !u) return fail(NR_EINVAL, "sampler or u is NULL");
+    NR_CUDA(cudaSetDevice(S->ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    nr_status r = sampler_eval(S, u, st);
+    if (r != NR_OK) return r;
+    CofitStageArgs a = stage_args(S, const_cast<double *>(u), kStageLogp);
+    a.logp_out = logp;
+    a.grad_out = grad;
+    cudaError_t e = launch_cofit_stage(a, st);
+    if (e != cudaSuccess) return fail(NR_ECUDA, "sampler stage: %s", cudaGetErrorString(e));
+    return NR_OK;
+}
+
+nr_status nr_hmc_step(nr_sampler *S, double *u, const double *z, const double *log_unif, const double *inv_mass,
+                      double eps, int32_t n_leapfrog, double *logp, int32_t *accepted, void *stream)
+{
+    if (!S || !u || !z || !log_unif || !inv_mass) return fail(NR_EINVAL, "sampler or array pointer is NULL");
+    if (n_leapfrog < 1) return fail(NR_EINVAL, "n_leapfrog %d < 1", n_leapfrog);
+    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(NR_EINVAL, "step %g not positive", eps);
+    NR_CUDA(cudaSetDevice(S->ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int l = 0; l <= n_leapfrog; ++l) {
+        nr_status r = sampler_eval(S, u, st);
+        if (r != NR_OK) return r;
+        CofitStageArgs a = stage_args(S, u, l == 0 ? kStageFirst : l == n_leapfrog ? kStageLast : kStageMid);
+        a.eps = eps;
+        a.inv_mass = inv_mass;
+        a.z = z;
+        a.log_unif = log_unif;
+        a.logp_out = logp;
+        a.accepted = accepted;
+        cudaError_t e = launch_cofit_stage(a, st);
+        if (e != cudaSuccess) return fail(NR_ECUDA, "sampler stage: %s", cudaGetErrorString(e));
     }
     return NR_OK;
 }

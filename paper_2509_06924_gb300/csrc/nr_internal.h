@@ -96,6 +96,32 @@ cudaError_t launch_profile(const double *params, const int64_t *par_off, const i
                            const float *z, int nz, float *rho_out, float *iota_out, int32_t *status, int sms,
                            cudaStream_t st);
 
+// ---- co-fit samplers (nr_hmc.cu) ----
+enum CofitStage : int { kStageLogp = 0, kStageFirst = 1, kStageMid = 2, kStageLast = 3 };
+struct CofitStageArgs {
+    int32_t C, P, NS, n_contrast; // chains, free parameters, packed slots per chain, contrasts per chain
+    int32_t stage;
+    double eps;                   // leapfrog step
+    double *u;                    // [C x P] unconstrained position (updated)
+    const double *ll;             // [C x n_contrast] log-likelihoods of the stacks
+    const double *gpk;            // [C x NS] packed likelihood gradient
+    const int32_t *tie_ptr;       // [P + 1] CSR over the slots that copy parameter k
+    const int32_t *tie_slot;
+    const double *lo, *hi;        // [P] prior bounds
+    const double *inv_mass;       // [P]
+    const double *z;              // [C x P] standard-normal momentum draws
+    const double *log_unif;       // [C] log of the uniform acceptance draws
+    double *mom;                  // [C x P] momentum (workspace)
+    double *u0;                   // [C x P] starting position (workspace)
+    double *H0, *logp0;           // [C] (workspace)
+    double *logp_out;             // [C] log pi of the resulting state (may be NULL)
+    double *grad_out;             // [C x P] d log pi / du (kStageLogp; may be NULL)
+    int32_t *accepted;            // [C] 1 accepted, 0 rejected (may be NULL)
+};
+cudaError_t launch_cofit_gather(const double *u, int C, int P, int NS, const int32_t *src, const double *val,
+                                const double *lo, const double *hi, double *params, cudaStream_t st);
+cudaError_t launch_cofit_stage(const CofitStageArgs &a, cudaStream_t st);
+
 // Raw per-stack sums of the mixed gradient kernels, and the stride of a
 // chunk's partial-sum slot: [accD (n) | accUr (n+1) | accUi (n+1) |
 // accS (n+1) | llsum | gscale | gbkg | gres].

@@ -293,6 +293,50 @@ def truth_stacks(name: str):
     return [n] * 3, _contrast_stacks(*_draw_layers(rng, n))
 
 
+def cofit_sampler_model(name: str):
+    """Sampler model of a co-fit workload ('oled_cofit' or 'vi_step'): the
+    three contrasts share every layer's thickness, SLD, absorption and the
+    roughnesses (tied slots); each contrast has its own free scale and
+    background; fronting and backing SLDs and the backing absorption stay
+    fixed.  Uniform priors: +-40 % (SLDs +-1.5e-6, absorption [0, 2e-8],
+    roughness [1, 30], scale [0.8, 1.2], background [1e-8, 1e-6]) around the
+    truth draw of the workload's data.  Returns (n_layers [3], dataset [3],
+    slot_src, slot_val, lo, hi, u_truth)."""
+    ns, stacks = truth_stacks(name)
+    n = ns[0]
+    L = layout(n)
+    d0, r0, i0, s0 = L["d"].start, L["rho"].start, L["iota"].start, L["sigma"].start
+    t = stacks[0]
+    lo, hi, truth = [], [], []
+
+    def free(lo_k, hi_k, v):
+        lo.append(lo_k)
+        hi.append(hi_k)
+        truth.append(v)
+        return len(lo) - 1
+    shared = {}
+    for j in range(n):
+        shared[d0 + j] = free(0.6 * t[d0 + j], 1.4 * t[d0 + j], t[d0 + j])
+        shared[r0 + 1 + j] = free(t[r0 + 1 + j] - 1.5e-6, t[r0 + 1 + j] + 1.5e-6, t[r0 + 1 + j])
+        shared[i0 + j] = free(0.0, 2e-8, min(max(t[i0 + j], 1e-10), 1.99e-8))
+    for j in range(n + 1):
+        shared[s0 + j] = free(1.0, 30.0, t[s0 + j])
+    src, val = [], []
+    for c, st in enumerate(stacks):
+        sc = free(0.8, 1.2, st[L["scale"]])
+        bk = free(1e-8, 1e-6, st[L["bkg"]])
+        s_c = -np.ones(4 * n + 6, np.int32)
+        for slot, k in shared.items():
+            s_c[slot] = k
+        s_c[L["scale"]], s_c[L["bkg"]] = sc, bk
+        src.append(s_c)
+        val.append(np.asarray(st, np.float64))
+    lo, hi, truth = np.array(lo), np.array(hi), np.array(truth)
+    u_truth = np.log((truth - lo) / (hi - truth))
+    return (np.array(ns, np.int32), np.arange(3, dtype=np.int32), np.concatenate(src), np.concatenate(val),
+            lo, hi, u_truth)
+
+
 def noise_rng(name: str):
     return np.random.Generator(np.random.PCG64(SEED_BASE + CONFIG_IDS[name] + 999331))
 

@@ -467,3 +467,86 @@ def test_sld_profile_sharp_steps_host_batch_and_flags():
     ctx.sld_profile(nr.Batch.from_workload(wl_bad), torch.as_tensor(z, device="cuda"))
     assert ctx.device_status() & nr.NR_FLAG_NONFINITE_PARAM
     ctx.close()
+
+
+# ------------------------------------------------------- on-device HMC step
+def sampler_setup(C=8, seed=7):
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_hmc import small_model
+    from oracle import hmc
+    model, u_t = small_model(seed)
+    # the device holds the data as float32: the reference uses the same values
+    f32 = lambda a: np.asarray(a, np.float32)
+    ref = hmc.Model(model.n_layers, model.dataset, model.slot_src, model.slot_val, model.lo, model.hi,
+                    model.q_off, f32(model.Q), f32(model.dQ), f32(model.Robs), f32(model.err), model.K)
+    ctx = nr.Context(n_quad=model.K)
+    dev = lambda a: torch.as_tensor(f32(a), device="cuda")
+    smp = nr.Sampler(ctx, C, model.n_layers, model.dataset, model.q_off, dev(model.Q), dev(model.dQ),
+                     dev(model.Robs), dev(model.err), model.slot_src, model.slot_val, model.lo, model.hi)
+    rng = np.random.default_rng(seed + 1)
+    u = u_t[None, :] + 0.2 * rng.normal(size=(C, model.P))
+    return ctx, smp, ref, u, rng
+
+
+def test_sampler_logp_grad_parity():
+    ctx, smp, ref, u, _ = sampler_setup()
+    lp, g = smp.logp_grad(torch.as_tensor(u, device="cuda"))
+    lp, g = lp.cpu().numpy(), g.cpu().numpy()
+    for c in range(u.shape[0]):
+        lr, gr = ref.logp_grad(u[c])
+        assert abs(lp[c] - lr) <= 1e-5 * abs(lr)
+        assert np.max(np.abs(g[c] - gr)) <= 1e-4 * np.max(np.abs(gr))
+    smp.close()
+    ctx.close()
+
+
+def test_hmc_step_parity_and_graph_replay():
+    C, P_eps, L = 8, 4e-4, 6
+    ctx, smp, ref, u, rng = sampler_setup(C)
+    z = rng.normal(size=(C, ref.P))
+    inv_mass = np.full(ref.P, 1.0)
+    # first half of the chains must accept, the rest reject: decisions that
+    # do not hinge on rounding; both branches of every kernel path run
+    log_u = np.where(np.arange(C) < C // 2, -np.inf, np.inf)
+    ud = torch.as_tensor(u, device="cuda")
+    lp, acc = smp.hmc_step(ud, torch.as_tensor(z, device="cuda"), torch.as_tensor(log_u, device="cuda"),
+                           torch.as_tensor(inv_mass, device="cuda"), P_eps, L)
+    assert ctx.device_status() == 0
+    ug, lp, acc = ud.cpu().numpy(), lp.cpu().numpy(), acc.cpu().numpy()
+    from oracle import hmc
+    for c in range(C):
+        ur, lr, ar, H0, H1 = hmc.hmc_step(ref.logp_grad, u[c], z[c], log_u[c], inv_mass, P_eps, L)
+        assert bool(acc[c]) == ar
+        assert abs(lp[c] - lr) <= 1e-5 * abs(lr)
+        # L leapfrog steps amplify the gradient's relative error by ~eps^2 L^2 |d2 log pi|
+        assert np.max(np.abs(ug[c] - ur)) <= 1e-6 + 1e-6 * np.max(np.abs(ur))
+    # the same step as a captured CUDA graph reproduces the eager result
+    u2 = torch.as_tensor(u, device="cuda")
+    zt, lt, mt = (torch.as_tensor(a, device="cuda") for a in (z, log_u, inv_mass))
+    lp2 = torch.empty(C, dtype=torch.float64, device="cuda")
+    acc2 = torch.empty(C, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        smp.hmc_step(u2, zt, lt, mt, P_eps, L, lp2, acc2, stream=s)    # warm-up (plans stay cached)
+    torch.cuda.synchronize()
+    u2.copy_(torch.as_tensor(u, device="cuda"))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        smp.hmc_step(u2, zt, lt, mt, P_eps, L, lp2, acc2, stream=s)
+    u2.copy_(torch.as_tensor(u, device="cuda"))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(u2.cpu(), torch.as_tensor(ug)) and torch.equal(acc2.cpu(), torch.as_tensor(acc))
+    smp.close()
+    ctx.close()
+
+
+def test_sampler_rejects_bad_models():
+    ctx = nr.Context(n_quad=17)
+    q = torch.ones(4, device="cuda")
+    with pytest.raises(nr.NRError):      # slot source out of range
+        nr.Sampler(ctx, 2, [0], [0], [0, 4], q, q, q, q, [5, -1, -1, -1, -1, -1], [0.0] * 6, [0.0], [1.0])
+    with pytest.raises(nr.NRError):      # empty prior box
+        nr.Sampler(ctx, 2, [0], [0], [0, 4], q, q, q, q, [0, -1, -1, -1, -1, -1], [0.0] * 6, [1.0], [1.0])
+    ctx.close()
