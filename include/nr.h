@@ -26,7 +26,7 @@
  *     (x_k, sqrt(pi) w_k) the K-point Gauss-Hermite rule;
  *   model m = scale * S + bkg (instrument parameters, Sec. 2.1);
  *   loglik = -1/2 sum_i [((m_i - R_i)/e_i)^2 + ln(2 pi e_i^2)] (Gaussian
- *     likelihood with count-derived deviations, Sec. 2.1; chi^2 of Eq. 20).
+ *     likelihood with count-derived deviations, Sec. 2.1; chi^2 of Eq. 25).
  *
  * Packed parameters of one stack with n layers: 4n+6 doubles
  *     d[n] | rho[n+2] | iota[n+1] | sigma[n+1] | scale | bkg
@@ -141,7 +141,7 @@ nr_status nr_plan(nr_ctx *ctx, const nr_batch *batch);
 nr_status nr_reflectivity(nr_ctx *ctx, const nr_batch *batch, float *r_out, void *stream);
 
 /* Gaussian log-likelihood of each stack against its dataset (Sec. 2.1;
- * chi^2 term of Eq. 20).  loglik: [S] doubles.  r_obs and r_err required. */
+ * chi^2 term of Eq. 25).  loglik: [S] doubles.  r_obs and r_err required. */
 nr_status nr_loglik(nr_ctx *ctx, const nr_batch *batch, double *loglik, void *stream);
 
 /* Log-likelihood and its gradient w.r.t. all packed parameters (the exact

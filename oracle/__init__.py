@@ -1,7 +1,7 @@
 """TEST INFRASTRUCTURE ONLY: ctypes wrapper around the plain CPU oracle
 (``nr_oracle.c``) for the batched neutron-reflectivity model of
 arXiv 2509.06924 (Abeles forward model, Sec. 2.1; Gaussian smearing, Sec. 3;
-Gaussian likelihood / chi^2, Sec. 2.1 and Eq. 20; exact gradient, Sec. 3).
+Gaussian likelihood / chi^2, Sec. 2.1 and Eq. 25; exact gradient, Sec. 3).
 
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA

@@ -23,7 +23,7 @@
  *    Gauss-Hermite quadrature;
  *  - model m = scale * S + bkg (theta_NR of Sec. 2.1; Tables 2 and 4);
  *  - Gaussian likelihood with per-point standard deviations (Sec. 2.1,
- *    text after Eq. 2), whose data term is the chi^2 of Eq. 20:
+ *    text after Eq. 2), whose data term is the chi^2 of Eq. 25:
  *      loglik = -1/2 sum_i [ ((m_i - R_i)/e_i)^2 + ln(2 pi e_i^2) ];
  *  - the gradient of loglik w.r.t. every packed parameter, by forward-mode
  *    dual numbers (one pass per parameter), the exact derivative the paper

@@ -1,7 +1,7 @@
 """GB300-native batched neutron reflectometry: the forward reflectivity model,
 its Gaussian log-likelihood and the exact gradient of that log-likelihood
 (arXiv 2509.06924: Abeles forward model, Sec. 2.1; refjax kernel interface and
-smearing, Sec. 3; chi^2 / Gaussian likelihood, Eq. 20 and Sec. 2.1), for many
+smearing, Sec. 3; chi^2 / Gaussian likelihood, Eq. 25 and Sec. 2.1), for many
 parameter samples at once, as HMC and variational inference need them.
 
 This module is the thin Python binding of the C-ABI library ``libnr.so``

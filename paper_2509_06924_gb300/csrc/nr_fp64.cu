@@ -1,6 +1,6 @@
 // nr_fp64.cu -- the plain FP64 path: the same forward model (Abeles /
 // Parratt with Nevot-Croce roughness, Sec. 2.1; Gauss-Hermite smearing,
-// Sec. 3; Gaussian likelihood, Sec. 2.1 / Eq. 20) written directly in
+// Sec. 3; Gaussian likelihood, Sec. 2.1 / Eq. 25) written directly in
 // complex double, one thread per (stack, Q point) looping over nodes and
 // layers.  It is the baseline the mixed path is measured against, and its
 // gradient is the central difference of the log-likelihood, each parameter
