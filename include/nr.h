@@ -299,6 +299,36 @@ nr_status nr_hmc_step(nr_sampler *sampler, double *u, const double *z, const dou
                       const double *inv_mass, double eps, int32_t n_leapfrog, double *logp, int32_t *accepted,
                       void *stream);
 
+/* ------------------------------------------------------------------------
+ * Variational inference with many independent restarts (Sec. 2.4; the LED
+ * co-fit of Sec. 4.2 runs restarts of a multivariate normal q in an
+ * unconstrained space, optimised by Adam).  The sampler's chains are the
+ * restarts: R = n_chains.  q(u; phi) = N(mu, L L^T) over the sampler's
+ * unconstrained coordinates.
+ *   phi:      [R x (P + P (P + 1) / 2)] DEVICE, per restart mu [P] then the
+ *             lower triangle of L row by row ((i, j <= i) at
+ *             i (i + 1) / 2 + j) with log L_ii on the diagonal; updated.
+ *   adam_m, adam_v: Adam's first and second moments, same shape (start at 0).
+ *   t:        DEVICE int32 counter of the iterations done (start at 0); the
+ *             call increments it on the device, so a captured call advances
+ *             it on every graph replay.
+ *   eps:      [R x P] DEVICE standard-normal draws, u = mu + L eps.
+ *   opt:      HOST Adam settings (lr > 0, 0 <= beta1, beta2 < 1, eps > 0).
+ *   elbo:     [R] DEVICE single-sample ELBO estimates at the incoming phi
+ *             (log pi(u) + eps^T eps / 2 + sum log L_ii + P/2 log 2 pi; may
+ *             be NULL).
+ * One iteration: u = mu + L eps, log pi and its gradient at u (one
+ * likelihood-gradient evaluation of R x n_contrasts stacks), the gradient of
+ * the single-sample negative ELBO (Eqs. 22-24) with eps held fixed, and one
+ * Adam step of every entry of phi.  No allocation or synchronisation: a
+ * step can be captured in a CUDA graph.  Errors: NR_EINVAL, NR_ECUDA. */
+typedef struct nr_adam {
+    double lr, beta1, beta2, eps;
+} nr_adam;
+
+nr_status nr_vi_step(nr_sampler *sampler, double *phi, double *adam_m, double *adam_v, int32_t *t,
+                     const double *eps, const nr_adam *opt, double *elbo, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

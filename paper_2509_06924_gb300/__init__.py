@@ -35,7 +35,7 @@ MAX_QUAD = 32
 EXPORTS = ("nr_create", "nr_destroy", "nr_last_error", "nr_plan", "nr_reflectivity", "nr_loglik",
            "nr_loglik_grad", "nr_loglik_grad_res", "nr_sld_profile", "nr_device_status", "nr_quadrature",
            "nr_plan_info", "nr_loglik_grad_noalloc", "nr_sampler_create", "nr_sampler_destroy",
-           "nr_sampler_logp_grad", "nr_hmc_step")
+           "nr_sampler_logp_grad", "nr_hmc_step", "nr_vi_step")
 NOALLOC_MAX_STACKS = 16384
 
 
@@ -66,6 +66,11 @@ class CCofitModel(ctypes.Structure):
                 ("q_off", ctypes.c_void_p), ("q", ctypes.c_void_p), ("dq", ctypes.c_void_p),
                 ("r_obs", ctypes.c_void_p), ("r_err", ctypes.c_void_p), ("slot_src", ctypes.c_void_p),
                 ("slot_val", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p)]
+
+
+class CAdam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
 
 
 _LIB = None
@@ -110,6 +115,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             lib.nr_sampler_destroy.restype = None
             lib.nr_sampler_logp_grad.argtypes = [vp, vp, vp, vp, vp]
             lib.nr_hmc_step.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, i32, vp, vp, vp]
+            lib.nr_vi_step.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(CAdam), vp, vp]
             for name in EXPORTS:
                 if name not in ("nr_destroy", "nr_last_error", "nr_sampler_destroy"):
                     getattr(lib, name).restype = ctypes.c_int
@@ -387,6 +393,30 @@ class Sampler:
                                      float(eps), int(n_leapfrog), ctypes.c_void_p(lp.data_ptr()),
                                      ctypes.c_void_p(acc.data_ptr()), _stream_handle(stream)))
         return lp, acc
+
+    def vi_step(self, phi, adam_m, adam_v, t, eps, lr=0.05, beta1=0.9, beta2=0.999, eps_adam=1e-8,
+                elbo_out=None, stream=None):
+        """One variational-inference iteration of every restart (the sampler's
+        chains): phi [R, P + P(P+1)/2] (mu, then the packed lower triangle of L
+        with log L_ii on its diagonal), Adam moments adam_m, adam_v of the same
+        shape, t a device int32 iteration counter, eps [R, P] standard-normal
+        draws.  Updates phi, the moments and t in place; returns the
+        single-sample ELBO estimates [R] at the incoming phi."""
+        import torch
+        elbo = elbo_out if elbo_out is not None else torch.empty(self.n_chains, dtype=torch.float64,
+                                                                  device=phi.device)
+        opt = CAdam(lr, beta1, beta2, eps_adam)
+        _check(self._lib.nr_vi_step(self._h, ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(adam_m.data_ptr()),
+                                    ctypes.c_void_p(adam_v.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                    ctypes.c_void_p(eps.data_ptr()), ctypes.byref(opt),
+                                    ctypes.c_void_p(elbo.data_ptr()), _stream_handle(stream)))
+        return elbo
+
+
+def vi_phi_size(P: int) -> int:
+    """Entries of one restart's variational parameters: mu [P] and the packed
+    lower triangle of L [P (P + 1) / 2]."""
+    return P + P * (P + 1) // 2
 
 
 def loglik_grad_noalloc(batch: Batch, n_quad: int, ll_out, grad_out, flags_out=None, stream=None) -> None:

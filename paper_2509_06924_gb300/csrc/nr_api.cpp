@@ -213,6 +213,7 @@ struct nr_sampler {
     std::vector<int64_t> q_off;
     nr_batch batch{};
     DevBuf d_src, d_val, d_lo, d_hi, d_tie_ptr, d_tie_slot, d_params, d_ll, d_gpk, d_mom, d_u0, d_H0, d_lp0;
+    DevBuf d_vu, d_vg, d_vlp, d_vpart; // variational step: u = mu + L e, d log pi / du, log pi, ELBO part
 };
 
 namespace {
@@ -785,6 +786,10 @@ nr_status nr_sampler_create(nr_ctx *ctx, const nr_cofit_model *m, nr_sampler **o
     NR_CUDA(S.d_u0.ensure(sizeof(double) * (size_t)C * P));
     NR_CUDA(S.d_H0.ensure(sizeof(double) * C));
     NR_CUDA(S.d_lp0.ensure(sizeof(double) * C));
+    NR_CUDA(S.d_vu.ensure(sizeof(double) * (size_t)C * P));
+    NR_CUDA(S.d_vg.ensure(sizeof(double) * (size_t)C * P));
+    NR_CUDA(S.d_vlp.ensure(sizeof(double) * C));
+    NR_CUDA(S.d_vpart.ensure(sizeof(double) * C));
     NR_CUDA(cudaMemcpy(S.d_src.p, m->slot_src, sizeof(int32_t) * NS, cudaMemcpyHostToDevice));
     NR_CUDA(cudaMemcpy(S.d_val.p, m->slot_val, sizeof(double) * NS, cudaMemcpyHostToDevice));
     NR_CUDA(cudaMemcpy(S.d_lo.p, m->lo, sizeof(double) * P, cudaMemcpyHostToDevice));
@@ -891,6 +896,33 @@ nr_status nr_hmc_step(nr_sampler *S, double *u, const double *z, const double *l
         cudaError_t e = launch_cofit_stage(a, st);
         if (e != cudaSuccess) return fail(NR_ECUDA, "sampler stage: %s", cudaGetErrorString(e));
     }
+    return NR_OK;
+}
+
+nr_status nr_vi_step(nr_sampler *S, double *phi, double *adam_m, double *adam_v, int32_t *t, const double *eps,
+                     const nr_adam *opt, double *elbo, void *stream)
+{
+    if (!S || !phi || !adam_m || !adam_v || !t || !eps || !opt) return fail(NR_EINVAL, "NULL argument");
+    if (!(opt->lr > 0.0) || !(opt->beta1 >= 0.0 && opt->beta1 < 1.0) || !(opt->beta2 >= 0.0 && opt->beta2 < 1.0) ||
+        !(opt->eps > 0.0))
+        return fail(NR_EINVAL, "Adam settings lr %g beta1 %g beta2 %g eps %g", opt->lr, opt->beta1, opt->beta2,
+                    opt->eps);
+    NR_CUDA(cudaSetDevice(S->ctx->device));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    double *u = S->d_vu.as<double>();
+    cudaError_t e = launch_vi_sample(phi, eps, S->C, S->P, u, S->d_vpart.as<double>(), t, st);
+    if (e != cudaSuccess) return fail(NR_ECUDA, "vi sample: %s", cudaGetErrorString(e));
+    nr_status r = sampler_eval(S, u, st);
+    if (r != NR_OK) return r;
+    CofitStageArgs a = stage_args(S, u, kStageLogp);
+    a.logp_out = S->d_vlp.as<double>();
+    a.grad_out = S->d_vg.as<double>();
+    e = launch_cofit_stage(a, st);
+    if (e == cudaSuccess)
+        e = launch_vi_adam(phi, adam_m, adam_v, eps, S->d_vg.as<double>(), S->d_vlp.as<double>(),
+                           S->d_vpart.as<double>(), S->C, S->P, t, opt->lr, opt->beta1, opt->beta2, opt->eps, elbo,
+                           st);
+    if (e != cudaSuccess) return fail(NR_ECUDA, "vi step: %s", cudaGetErrorString(e));
     return NR_OK;
 }
 

@@ -121,6 +121,12 @@ struct CofitStageArgs {
 cudaError_t launch_cofit_gather(const double *u, int C, int P, int NS, const int32_t *src, const double *val,
                                 const double *lo, const double *hi, double *params, cudaStream_t st);
 cudaError_t launch_cofit_stage(const CofitStageArgs &a, cudaStream_t st);
+// variational inference (nr_vi.cu)
+cudaError_t launch_vi_sample(const double *phi, const double *eps, int R, int P, double *u, double *part,
+                             int32_t *t_dev, cudaStream_t st);
+cudaError_t launch_vi_adam(double *phi, double *m, double *v, const double *eps, const double *g,
+                           const double *logp, const double *part, int R, int P, const int32_t *t_dev, double lr,
+                           double beta1, double beta2, double eps_adam, double *elbo, cudaStream_t st);
 
 // Raw per-stack sums of the mixed gradient kernels, and the stride of a
 // chunk's partial-sum slot: [accD (n) | accUr (n+1) | accUi (n+1) |

@@ -1,0 +1,115 @@
+// nr_vi.cu -- variational inference for a co-fitted slab model on the GPU,
+// many independent restarts at once (arXiv 2509.06924, Sec. 2.4; the LED
+// co-fit of Sec. 4.2 runs 100 restarts of a multivariate normal q in an
+// unconstrained space, optimised by Adam).
+//
+// phi of one restart: mu [P] and the lower triangle of the Cholesky factor L,
+// packed row by row ((i, j <= i) at i (i + 1) / 2 + j) with log L_ii on the
+// diagonal.  One iteration with a standard-normal draw e (an input):
+//   vi_sample: u = mu + L e, and the part of the ELBO estimate that does not
+//              involve the likelihood, e^T e / 2 + sum_i log L_ii + P/2 log 2 pi
+//              (one warp per restart);
+//   the co-fit sampler's log pi(u) and gradient g (gather, mixed gradient
+//   kernel, pull-back);
+//   vi_adam:   the gradient of the single-sample negative ELBO (Eqs. 22-24,
+//              e held fixed: d/d mu = -g, d/d L_ij = -g_i e_j,
+//              d/d log L_ii = -g_i e_i L_ii - 1) and one Adam step of every
+//              entry of phi, one thread per entry; the ELBO estimate
+//              log pi(u) + (the part above) is written per restart.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "nr_internal.h"
+
+namespace nrimpl {
+namespace {
+
+constexpr unsigned kMask = 0xffffffffu;
+constexpr double kHalfLog2Pi = 0.91893853320467274178032973640562; // ln(2 pi) / 2
+
+__global__ void vi_sample_kernel(const double *phi, const double *eps, int R, int P, int64_t nphi, double *u,
+                                 double *part, int32_t *t_dev)
+{
+    const int warps = blockDim.x >> 5;
+    const int r = blockIdx.x * warps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    // the iteration counter lives on the device, so a captured iteration
+    // advances it on every replay; vi_adam (later in the stream) reads it
+    if (blockIdx.x == 0 && threadIdx.x == 0) *t_dev += 1;
+    if (r >= R) return;
+    const double *mu = phi + (int64_t)r * nphi;
+    const double *tri = mu + P;
+    const double *e = eps + (int64_t)r * P;
+    double acc = 0.0;
+    for (int i = lane; i < P; i += 32) {
+        const double *row = tri + (int64_t)i * (i + 1) / 2;
+        double ui = mu[i] + exp(row[i]) * e[i];
+        for (int j = 0; j < i; ++j) ui += row[j] * e[j];
+        u[(int64_t)r * P + i] = ui;
+        acc += 0.5 * e[i] * e[i] + row[i] + kHalfLog2Pi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kMask, acc, o);
+    if (lane == 0) part[r] = acc;
+}
+
+__global__ void vi_adam_kernel(double *phi, double *m, double *v, const double *eps, const double *g,
+                               const double *logp, const double *part, int R, int P, int64_t nphi,
+                               const int32_t *t_dev, double lr, double beta1, double beta2, double eps_adam,
+                               double *elbo)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)R * nphi) return;
+    const int r = (int)(idx / nphi);
+    const int64_t p = idx - (int64_t)r * nphi;
+    const double *gr = g + (int64_t)r * P;
+    double grad;
+    if (p < P) {
+        grad = -gr[p];
+    } else {
+        // packed triangle index -> (i, j): i (i + 1) / 2 <= q < (i + 1) (i + 2) / 2
+        const int64_t q = p - P;
+        int i = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+        while ((int64_t)(i + 1) * (i + 2) / 2 <= q) ++i;
+        while ((int64_t)i * (i + 1) / 2 > q) --i;
+        const int j = (int)(q - (int64_t)i * (i + 1) / 2);
+        const double *e = eps + (int64_t)r * P;
+        grad = (i == j) ? -gr[i] * e[i] * exp(phi[idx]) - 1.0 : -gr[i] * e[j];
+    }
+    const double mm = beta1 * m[idx] + (1.0 - beta1) * grad;
+    const double vv = beta2 * v[idx] + (1.0 - beta2) * grad * grad;
+    m[idx] = mm;
+    v[idx] = vv;
+    const double t = (double)*t_dev;
+    const double mh = mm / (1.0 - pow(beta1, t));
+    const double vh = vv / (1.0 - pow(beta2, t));
+    phi[idx] -= lr * mh / (sqrt(vh) + eps_adam);
+    if (p == 0 && elbo) elbo[r] = logp[r] + part[r];
+}
+
+} // namespace
+
+cudaError_t launch_vi_sample(const double *phi, const double *eps, int R, int P, double *u, double *part,
+                             int32_t *t_dev, cudaStream_t st)
+{
+    if (R == 0) return cudaSuccess;
+    const int64_t nphi = (int64_t)P + (int64_t)P * (P + 1) / 2;
+    vi_sample_kernel<<<(R + 3) / 4, 128, 0, st>>>(phi, eps, R, P, nphi, u, part, t_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vi_adam(double *phi, double *m, double *v, const double *eps, const double *g,
+                           const double *logp, const double *part, int R, int P, const int32_t *t_dev, double lr,
+                           double beta1, double beta2, double eps_adam, double *elbo, cudaStream_t st)
+{
+    const int64_t nphi = (int64_t)P + (int64_t)P * (P + 1) / 2;
+    const int64_t n = (int64_t)R * nphi;
+    if (n == 0) return cudaSuccess;
+    vi_adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(phi, m, v, eps, g, logp, part, R, P, nphi, t_dev,
+                                                                 lr, beta1, beta2, eps_adam, elbo);
+    return cudaGetLastError();
+}
+
+} // namespace nrimpl

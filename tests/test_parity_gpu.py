@@ -550,3 +550,55 @@ def test_sampler_rejects_bad_models():
     with pytest.raises(nr.NRError):      # empty prior box
         nr.Sampler(ctx, 2, [0], [0], [0, 4], q, q, q, q, [0, -1, -1, -1, -1, -1], [0.0] * 6, [1.0], [1.0])
     ctx.close()
+
+
+# ---------------------------------------------- variational-inference step
+def test_vi_step_parity_and_graph_replay():
+    from oracle import vi
+    R = 6
+    ctx, smp, ref, u_c, rng = sampler_setup(R, seed=11)
+    P = ref.P
+    nphi = nr.vi_phi_size(P)
+    phi = np.zeros((R, nphi))
+    phi[:, :P] = u_c                                   # mu: the chains' starting points
+    for r in range(R):                                 # L = 0.1 I plus a little correlation
+        idx = P
+        for i in range(P):
+            for j in range(i + 1):
+                phi[r, idx] = np.log(0.1) if i == j else 0.02 * rng.normal()
+                idx += 1
+    m0 = 0.01 * np.abs(rng.normal(size=(R, nphi)))
+    v0 = 0.001 * np.abs(rng.normal(size=(R, nphi)))
+    eps = rng.normal(size=(R, P))
+    t0 = 4                                             # iterations already done
+    dev = lambda a: torch.as_tensor(a, device="cuda")
+    ph, m, v, t = dev(phi), dev(m0), dev(v0), dev(np.array([t0], np.int32))
+    elbo = smp.vi_step(ph, m, v, t, dev(eps), lr=0.05)
+    assert ctx.device_status() == 0 and int(t.item()) == t0 + 1
+    ph, m, v, elbo = ph.cpu().numpy(), m.cpu().numpy(), v.cpu().numpy(), elbo.cpu().numpy()
+    for r in range(R):
+        mu_r, tri_r, m_r, v_r, el_r = vi.vi_step(ref.logp_grad, phi[r, :P], phi[r, P:], m0[r], v0[r], t0 + 1,
+                                                 eps[r], 0.05)
+        assert abs(elbo[r] - el_r) <= 1e-5 * abs(el_r)
+        # the gradient carries the mixed path's ~1e-5 relative error; Adam's
+        # step is lr * mhat / sqrt(vhat): its error stays a small fraction of lr
+        np.testing.assert_allclose(ph[r], np.concatenate([mu_r, tri_r]), rtol=0, atol=2e-3 * 0.05)
+        np.testing.assert_allclose(m[r], m_r, rtol=1e-4, atol=1e-9 * np.max(np.abs(m_r)))
+    # a captured iteration replays with the device counter advancing
+    ph2, m2, v2, t2, e2 = dev(phi), dev(m0), dev(v0), dev(np.array([t0], np.int32)), dev(eps)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        smp.vi_step(ph2, m2, v2, t2, e2, stream=s)
+    torch.cuda.synchronize()
+    ph2.copy_(dev(phi)); m2.copy_(dev(m0)); v2.copy_(dev(v0)); t2.fill_(t0)
+    graph = torch.cuda.CUDAGraph()
+    el2 = torch.empty(R, dtype=torch.float64, device="cuda")
+    with torch.cuda.graph(graph, stream=s):
+        smp.vi_step(ph2, m2, v2, t2, e2, elbo_out=el2, stream=s)
+    ph2.copy_(dev(phi)); m2.copy_(dev(m0)); v2.copy_(dev(v0)); t2.fill_(t0)
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert int(t2.item()) == t0 + 2
+    smp.close()
+    ctx.close()
