@@ -622,6 +622,8 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     const int qs0 = (warp * 32) / K;
     const int nslots = (31 + K - 1) / K + 1; // most slots any warp touches
     const int sgl = nslots <= 1 ? 32 : nslots <= 2 ? 16 : nslots <= 4 ? 8 : nslots <= 8 ? 4 : nslots <= 16 ? 2 : 1;
+    // widest node offset |g_k|: the nodes of a Q point lie within Q/2 +- |dQ/2| g_max
+    const float g_max = fmaxf(fabsf(qc.g_hi[0]), fabsf(qc.g_hi[K - 1]));
 
     for (int i = tid; i < 4 * BLOCK; i += BLOCK) (&sh_wR[0][0])[i] = 0.f; // padding stays 0
 
@@ -733,7 +735,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 ll_hi = t1;
                 ll_lo += t2;
                 if constexpr (GRAD) {
-                    const float dldm = -(rs.x * sh_qd[i].w);
+                    const float dldm = -(rs.x * fabsf(sh_qd[i].w));
                     gsc_acc = fmaf(dldm, rs.y, gsc_acc);
                     gbk_acc += dldm;
                 }
@@ -753,6 +755,21 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     if (LIK) {
                         v.z = __ldg(rop + qa);
                         v.w = rcp_approx(__ldg(rep + qa));
+                    }
+                    if constexpr (GRAD) {
+                        // can a node of this Q point reach the interior-edge band
+                        // |k_j|^2 < f k_0^2 of a layer (k_0^2 within c_j / (1 +- f))?
+                        // The sign of 1/err carries the answer (negative: yes).
+                        const float a = fabsf(v.y) * g_max;
+                        const float lo = fmaxf(v.x - a, 0.f), hi = v.x + a;
+                        const float k2lo = lo * lo * (1.f - 1.5f * kEdgeFrac);
+                        const float k2hi = hi * hi * (1.f + 1.5f * kEdgeFrac);
+                        bool e = false;
+                        for (int j = 1; j <= n; ++j) {
+                            const float c = sm.med[j].x;
+                            e |= c > 0.f && c < k2hi && c > k2lo;
+                        }
+                        if (e && v.w > 0.f) v.w = -v.w;
                     }
                 }
                 sh_qd[i] = v;
@@ -878,9 +895,10 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 if (act && kn == 0) ka.r_out[si.out_off + qi] = fmaf(scale, S, bkg);
             } else {
                 const float m = fmaf(scale, S, bkg);
-                const float res = (m - qd.z) * qd.w; // (m - R) / err
+                const float ie = fabsf(qd.w);
+                const float res = (m - qd.z) * ie; // (m - R) / err
                 if (act && kn == 0) sh_rs[si_q] = make_float2(res, S);
-                if constexpr (GRAD) Rb = wks * -(res * qd.w); // w_k scale dl/dm (0 on idle lanes)
+                if constexpr (GRAD) Rb = wks * -(res * ie); // w_k scale dl/dm (0 on idle lanes)
             }
             if constexpr (GRAD) {
                 // a7: adjoint sweep from the fronting down to the backing
@@ -901,7 +919,9 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     acc_add(oUi + idx, im);
                     if constexpr (RES) res_sum += re;
                 };
-                auto adj_step = [&](int j, auto TOP, auto BOT) __attribute__((always_inline)) {
+                // EDG: the warp's tile may hold interior-edge evaluations (else
+                // the edge test and its queue are compiled out of the sweep)
+                auto adj_step = [&](int j, auto TOP, auto BOT, auto EDG) __attribute__((always_inline)) {
                     const bool top = pos_flag(TOP, j == 0), bot = pos_flag(BOT, j == n);
                     const float4 Ij = sm.itf[j];
                     const float4 Lj1 = sm.lay[j + 1]; // layer j+1 (zeros past the last layer)
@@ -980,8 +1000,8 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         // k_j complete: accumulate conj(kbar) / k_j, or queue
                         // the interior-edge evaluation for this lane
                         const float m2 = fmaf(kj.re, kj.re, kj.im * kj.im);
-                        const bool edge = act && m2 < edge_u;
-                        const unsigned em = __ballot_sync(kFull, edge);
+                        const bool edge = decltype(EDG)::value && act && m2 < edge_u;
+                        const unsigned em = decltype(EDG)::value ? __ballot_sync(kFull, edge) : 0u;
                         if (em) {
                             if (edge) {
                                 const int slot = eq_cnt + __popc(em & ((1u << lane) - 1u));
@@ -1024,21 +1044,29 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         acc_u_nonedge(j, kk.x * inv, -kk.y * inv);
                     }
                 };
-                if constexpr (T::UNROLL) {
+                auto sweep = [&](auto EDG) __attribute__((always_inline)) {
+                    if constexpr (T::UNROLL) {
 #pragma unroll
-                    for (int j = 0; j <= NM; ++j)
-                        if (j <= n) adj_step(j, Pos<kRt>{}, Pos<kRt>{});
-                    // drain full batches of the interior-edge queue
-                    while (eq_cnt >= 32) {
-                        __syncwarp();
-                        eq_drain(32);
-                    }
-                } else {
-                    if (n >= 1) adj_step(0, Pos<kYes>{}, Pos<kNo>{});
+                        for (int j = 0; j <= NM; ++j)
+                            if (j <= n) adj_step(j, Pos<kRt>{}, Pos<kRt>{}, EDG);
+                        // drain full batches of the interior-edge queue
+                        if constexpr (decltype(EDG)::value) {
+                            while (eq_cnt >= 32) {
+                                __syncwarp();
+                                eq_drain(32);
+                            }
+                        }
+                    } else {
+                        if (n >= 1) adj_step(0, Pos<kYes>{}, Pos<kNo>{}, EDG);
 #pragma unroll kDeepUnroll
-                    for (int j = 1; j <= n - 1; ++j) adj_step(j, Pos<kNo>{}, Pos<kNo>{});
-                    adj_step(n, Pos<kRt>{}, Pos<kYes>{});
-                }
+                        for (int j = 1; j <= n - 1; ++j) adj_step(j, Pos<kNo>{}, Pos<kNo>{}, EDG);
+                        adj_step(n, Pos<kRt>{}, Pos<kYes>{}, EDG);
+                    }
+                };
+                // the staged sign of 1/err marks Q points whose nodes may reach
+                // an interior-edge band (warp-uniform choice)
+                if (__any_sync(kFull, act && qd.w < 0.f)) sweep(std::true_type{});
+                else sweep(std::false_type{});
                 if constexpr (RES) gres_acc = fmaf(wres, fmaf(k0h, res_sum, res_k0), gres_acc);
             }
         }
