@@ -584,7 +584,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     constexpr int EQ = T::EQ_CAP;
 
     __shared__ StackSmem<NM> sm;
-    __shared__ float sh_wR[2][2 * BLOCK]; // w_k R per (Q slot, node), double-buffered
+    __shared__ __align__(16) float sh_wR[2][2 * BLOCK]; // w_k R per (Q slot, node), double-buffered
     // the super-tile's data per Q point: (Q/2, dQ/2, R_obs, 1/err), and the
     // (residual, smeared R) pairs its tiles leave for the likelihood sums
     __shared__ float4 sh_qd[T::CAPQ];
@@ -608,7 +608,9 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int K = KC > 0 ? KC : qc.K; // KC: quadrature order fixed at compile time (0: runtime)
-    const int KP = K;            // node stride of a Q slot in sh_wR
+    // node stride of a Q slot in sh_wR: K rounded up to whole float4s (the
+    // padding stays 0), so a slot's values are read 4 at a time
+    const int KP = (K + 3) & ~3;
     const int TQ = ka.tile_q;
     const int qslot = tid / K;
     const int kn = tid - qslot * K;
@@ -886,8 +888,24 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 const int g = lane / sgl, part = lane - g * sgl;
                 const int slot = qs0 + g;
                 float ps = 0.f;
-                if (slot < TQ)
-                    for (int k = part; k < K; k += sgl) ps += sh_wR[buf][slot * KP + k];
+                if (slot < TQ) {
+                    const float4 *row = reinterpret_cast<const float4 *>(&sh_wR[buf][slot * KP]);
+                    auto add4 = [&](int c) __attribute__((always_inline)) {
+                        const float4 v = row[c];
+                        ps += (v.x + v.y) + (v.z + v.w);
+                    };
+                    if constexpr (KC > 0) {
+                        // compile-time trip count: the strided float4s of this part
+                        constexpr int NSL = (31 + KC - 1) / KC + 1;
+                        constexpr int SGL = NSL <= 1 ? 32 : NSL <= 2 ? 16 : NSL <= 4 ? 8 : NSL <= 8 ? 4
+                                                                                : NSL <= 16 ? 2 : 1;
+#pragma unroll
+                        for (int i = 0; i < ((KC + 3) / 4 + SGL - 1) / SGL; ++i)
+                            if (part + i * SGL < (KC + 3) / 4) add4(part + i * SGL);
+                    } else {
+                        for (int c = part; c < KP / 4; c += sgl) add4(c);
+                    }
+                }
                 for (int o = 1; o < sgl; o <<= 1) ps += __shfl_xor_sync(kFull, ps, o);
                 S = __shfl_sync(kFull, ps, ((qslot - qs0) * sgl) & 31);
             }
