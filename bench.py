@@ -156,9 +156,16 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+KERNEL_SOURCES = ("nr_device.cuh", "nr_mixed.cu", "nr_pair.cu")
+
+
 def kernel_source_hash() -> str:
-    src = os.path.join(ROOT, "paper_2509_06924_gb300", "csrc", "nr_mixed.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the gradient kernels' sources (shared header, one- and
+    two-evaluations-per-thread kernels), in that order."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2509_06924_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def profile_record(workload: str) -> dict:
@@ -400,6 +407,24 @@ def vi_measure(nr, W, dev, restarts=100, iters=2000, lr=0.005, scale0=0.01, tail
     return out
 
 
+def time_device(fn, steps: int, flush, stream) -> float:
+    """Mean device time (ms) of fn() over `steps` calls, L2 flushed before
+    each, CUDA events on the launching stream; 3 warm-up calls first."""
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        fn()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / steps
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -474,6 +499,20 @@ def run_ours(args):
         e2e = {"value": ws * wl.evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    # forward-only paths on the same batch: the log-likelihood (model, smearing
+    # and likelihood, no adjoint) and the smeared model alone
+    fwd = None
+    if not args.no_forward:
+        m_out = torch.empty(batch.total_out, dtype=torch.float32, device=dev)
+        n_fwd = max(5, min(args.steps, 50))
+        ms_ll = max_over_ranks(time_device(lambda: ctx.loglik(batch, out=ll, stream=stream), n_fwd, flush,
+                                           stream), dev)
+        ms_r = max_over_ranks(time_device(lambda: ctx.reflectivity(batch, out=m_out, stream=stream), n_fwd,
+                                          flush, stream), dev)
+        fwd = {"loglik": {"value": ws * evals / (ms_ll * 1e-3), "unit": UNIT, "ms_per_call": ms_ll},
+               "reflectivity": {"value": ws * evals / (ms_r * 1e-3), "unit": UNIT, "ms_per_call": ms_r},
+               "steps": n_fwd}
+
     status = ctx.device_status()
     if status != 0:
         raise RuntimeError(f"device status flags {status}")
@@ -484,6 +523,9 @@ def run_ours(args):
 
     flops = sum(flops_per_eval(int(n), wl.n_quad) * (wl.out_off[s + 1] - wl.out_off[s]) * wl.n_quad
                 for s, n in enumerate(wl.n_layers))
+    # layer-evaluations weight each evaluation by its interface count n + 1
+    layer_evals = sum((int(n) + 1) * (wl.out_off[s + 1] - wl.out_off[s]) * wl.n_quad
+                      for s, n in enumerate(wl.n_layers))
     kernel_ms = ms  # the step is one launch of the gradient kernel per layer bucket
     achieved = flops / (kernel_ms * 1e-3) / 1e12
     peak = peak_fp32_tflops()
@@ -501,6 +543,8 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)"},
         "e2e": e2e,
+        "layer_evals_per_s": ws * layer_evals / (ms * 1e-3),
+        "forward": fwd,
         "fp64_fd_baseline": None if args.no_cpu_baseline else fp64_fd_baseline(wl),
         "gpu_launches": int(info["launches"]) * args.steps,
         "clocks": clk.summary(),
@@ -534,6 +578,7 @@ def main():
     ap.add_argument("--workload", default="thick_oxide")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement (profiling runs)")
+    ap.add_argument("--no-forward", action="store_true", help="skip the forward-only timings (profiling runs)")
     ap.add_argument("--no-infer", action="store_true",
                     help="skip the on-device HMC transition and VI run (profiling runs)")
     ap.add_argument("--stacks", type=int, default=None,

@@ -15,9 +15,9 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libnr.so")
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["nr_mixed.cu", "nr_fp64.cu", "nr_noalloc.cu", "nr_profile.cu", "nr_hmc.cu", "nr_vi.cu"]
+CU_SOURCES = ["nr_mixed.cu", "nr_pair.cu", "nr_fp64.cu", "nr_noalloc.cu", "nr_profile.cu", "nr_hmc.cu", "nr_vi.cu"]
 CPP_SOURCES = ["nr_api.cpp"]
-HEADERS = ["nr_internal.h"]
+HEADERS = ["nr_internal.h", "nr_device.cuh"]
 
 
 def _cuda_home() -> str:

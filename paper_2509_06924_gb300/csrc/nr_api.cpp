@@ -267,8 +267,7 @@ bool same_meta(const Plan &p, const nr_batch *b, int K)
 
 int tile_for(const nr_ctx *ctx, int mode, int nmax)
 {
-    const int block = mixed_block_threads(mode, nmax);
-    int tq = std::min(block / ctx->qc.K, block / kSubLanes);
+    int tq = mixed_tile_q(mode, nmax, ctx->qc.K);
     if (ctx->opt.tile_q > 0) tq = std::min(tq, ctx->opt.tile_q);
     return std::max(tq, 1);
 }

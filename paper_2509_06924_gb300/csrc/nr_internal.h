@@ -1,5 +1,5 @@
 // nr_internal.h -- structures shared by the host API (nr_api.cpp) and the
-// CUDA kernels (nr_mixed.cu, nr_fp64.cu) of the reflectivity library.
+// CUDA kernels (nr_mixed.cu, nr_pair.cu, nr_fp64.cu, ...) of the reflectivity library.
 #pragma once
 
 #include <cstdint>
@@ -80,11 +80,21 @@ struct KernelArgs {
 // the launch (every stack of the launch has n <= nmax; nmax = 1 means exactly
 // one layer); 0 selects the runtime-n forward kernel (model / loglik modes).
 int mixed_block_threads(int mode, int nmax);
+// most Q points per CTA tile of a launch (quadrature order K)
+int mixed_tile_q(int mode, int nmax, int K);
 size_t mixed_dyn_smem(int mode, int nmax);
 cudaError_t mixed_occupancy(int mode, int nmax, int K, int *blocks_per_sm);
 cudaError_t launch_mixed(int mode, int nmax, int grid, const KernelArgs &a, const QuadConst &qc,
                          cudaStream_t st);
 bool mixed_bucket_ok(int mode, int nmax);
+
+// ---- paired gradient kernel (nr_pair.cu): two evaluations per thread ----
+// Used by launch_mixed / mixed_occupancy / mixed_tile_q for the 1- and
+// 2-layer gradient buckets when K >= 3.
+bool pair_eligible(int mode, int nmax, int K);
+int pair_block_threads();
+cudaError_t pair_occupancy(int mode, int nmax, int K, int *blocks_per_sm);
+cudaError_t launch_pair(int mode, int nmax, int grid, const KernelArgs &a, const QuadConst &qc, cudaStream_t st);
 
 // ---- launchers (nr_fp64.cu) ----
 constexpr int kFp64Block = 128;

@@ -235,12 +235,11 @@ extern "C" nr_status nr_loglik_grad_noalloc(const nr_batch *b, int32_t n_quad, d
     for (int g = 0; g < kNumBuckets; ++g) {
         if (count[g] == 0) continue;
         const int nmax = kBuckets[g];
-        const int block = mixed_block_threads(kGrad, nmax);
         int occ = 1;
         if (mixed_occupancy(kGrad, nmax, n_quad, &occ) != cudaSuccess) return err(NR_ECUDA, "occupancy query failed");
         a.items = d_items + first;
         a.n_items = count[g];
-        a.tile_q = std::max(1, std::min(block / n_quad, block / kSubLanes));
+        a.tile_q = std::max(1, mixed_tile_q(kGrad, nmax, n_quad));
         a.ticket = d_tickets + 2 * g;
         const int grid = std::max(1, std::min(count[g], sms * std::max(occ, 1)));
         if (launch_mixed(kGrad, nmax, grid, a, qc, st) != cudaSuccess) return err(NR_ECUDA, "kernel launch failed");
