@@ -21,7 +21,7 @@
 // intermediates (1-2 layers keep all of them in registers) and the same
 // interior critical-edge treatment: evaluations whose k_j falls in the edge
 // band are queued per warp and drained by the scalar edge adjoint, one entry
-// per lane.  Thread t carries evaluations 2t and 2t+1 of its tile.
+// per lane.  A thread carries two adjacent evaluation slots of its tile.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -252,16 +252,24 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
     const int K = KC > 0 ? KC : qc.K; // K >= 3 (the host's choice of this kernel)
     const int KP = (K + 3) & ~3;      // node stride of a Q slot in sh_wR (whole float4s)
     const int TQ = ka.tile_q;
-    // the thread's two evaluations: tile slots 2 tid + h
+    // Warp-local tiles: when every warp's 64 evaluation slots hold whole Q
+    // points and the CTA tile is exactly those (TQ = warps x floor(64/K), no
+    // slot lost against the CTA-wide layout, e.g. K = 21: 4 x 3 Q points),
+    // each warp owns its Q slots and the smearing exchange needs only a warp
+    // barrier.  Otherwise the thread carries tile slots 2 tid + h and the
+    // exchange takes a CTA barrier.
+    const int tqw = 64 / K;
+    const bool wloc = TQ == WARPS * tqw;
     int qslot[2], kn[2];
     bool lane_on[2];
     f2 g_hi, g_lo, wk;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int e = 2 * tid + h;
-        qslot[h] = e / K;
-        kn[h] = e - qslot[h] * K;
-        lane_on[h] = qslot[h] < TQ;
+        const int e = wloc ? 2 * lane + h : 2 * tid + h;
+        const int ls = e / K;
+        kn[h] = e - ls * K;
+        qslot[h] = wloc ? warp * tqw + ls : ls;
+        lane_on[h] = wloc ? ls < tqw : ls < TQ;
         const float gh = lane_on[h] ? qc.g_hi[kn[h]] : 0.f;
         const float gl = lane_on[h] ? qc.g_lo[kn[h]] : 0.f;
         const float w = lane_on[h] ? qc.w[kn[h]] : 0.f;
@@ -269,8 +277,10 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
         else { g_hi.y = gh; g_lo.y = gl; wk.y = w; }
     }
     // smearing sums: the warp's 64 evaluations touch Q slots qs0.. (at most
-    // nslots of them); sgl lanes per slot (depends on K only)
-    const int qs0 = (warp * 64) / K;
+    // nslots of them; exactly tqw with warp-local tiles, and only those are
+    // summed); sgl lanes per slot (depends on K only)
+    const int qs0 = wloc ? warp * tqw : (warp * 64) / K;
+    const int qs_end = wloc ? qs0 + tqw : TQ;
     const int nslots = (63 + K - 1) / K + 1;
     const int sgl = nslots <= 1 ? 32 : nslots <= 2 ? 16 : nslots <= 4 ? 8 : nslots <= 8 ? 4 : nslots <= 16 ? 2 : 1;
     const float g_max = fmaxf(fabsf(qc.g_hi[0]), fabsf(qc.g_hi[K - 1]));
@@ -454,13 +464,14 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
 #pragma unroll
             for (int h = 0; h < 2; ++h)
                 if (lane_on[h]) sh_wR[buf][qslot[h] * KP + kn[h]] = half(wk, h) * half(R, h);
-            __syncthreads();
+            if (wloc) __syncwarp();
+            else __syncthreads();
             f2 S;
             {
                 const int g = lane / sgl, part = lane - g * sgl;
                 const int slot = qs0 + g;
                 float ps = 0.f;
-                if (slot < TQ) {
+                if (slot < qs_end) {
                     const float4 *row = reinterpret_cast<const float4 *>(&sh_wR[buf][slot * KP]);
                     auto add4 = [&](int c) __attribute__((always_inline)) {
                         const float4 v = row[c];

@@ -241,6 +241,37 @@ def test_quadrature_orders(K):
     assert_parity(wl, run_gpu(wl), run_oracle(wl))
 
 
+# The 1- and 2-layer gradient buckets (n = 0, 1, 2) run two evaluations per
+# thread when K >= 3; a warp's 64 evaluations straddle Q slots differently
+# for every K.  Stacks with films denser than the substrate put nodes in the
+# interior critical-edge band (the per-warp queue); the second dataset is
+# dense around those edges.
+@pytest.mark.parametrize("K", [3, 4, 5, 7, 13, 31])
+def test_paired_gradient_kernel_orders_and_buckets(K):
+    rng = np.random.default_rng(100 + K)
+    q1, q2 = W.log_grid(61, 0.004, 0.3), W.log_grid(29, 0.008, 0.03)
+    datasets = [(q1, 0.05 * q1), (q2, 0.06 * q2)]
+    stacks = [(1, rand_stack(rng, 1), 0), (2, rand_stack(rng, 2), 1),
+              (0, W.pack([], [0.0, 2.07e-6], [0.0], [3.0], 1.0, 1e-7), 0),
+              (2, W.pack([300.0, 150.0], [0.0, 6.0e-6, 4.5e-6, 2.07e-6], [0.0, 0.0, 0.0], [3.0, 5.0, 4.0],
+                         1.0, 1e-7), 1),
+              (1, W.pack([900.0], [0.0, 5.0e-6, 2.07e-6], [2e-9, 0.0], [4.0, 6.0], 1.0, 1e-7), 1),
+              (1, rand_stack(rng, 1), 1)]
+    wl = custom_workload(stacks, datasets, K=K)
+    ref_ll, ref_g, ref_r = oracle.batch("grad_res", wl.n_layers, wl.params, wl.dataset, wl.q_off, wl.q, wl.dq,
+                                        wl.r_obs, wl.r_err, K)
+    ref = {"ll": ref_ll, "g": ref_g}
+    assert_parity(wl, run_gpu(wl, modes=("grad",)), ref)
+    # several items per stack and a tile shorter than the widest, with the
+    # resolution derivative through the same kernel
+    ctx = nr.Context(n_quad=K, chunk_q=9, tile_q=5)
+    ll, g, gr = (t.cpu().numpy() for t in ctx.loglik_grad_res(nr.Batch.from_workload(wl)))
+    assert ctx.device_status() == 0
+    ctx.close()
+    assert np.max(np.abs(ll - ref_ll) / np.abs(ref_ll)) <= TOL_LL
+    assert res_err(wl, g, gr, ref_g, ref_r) <= TOL_G
+
+
 def test_zero_resolution_is_unsmeared():
     wl = W.make_workload("thick_oxide", n_stacks=16)
     wl.dq = np.zeros_like(wl.dq)
