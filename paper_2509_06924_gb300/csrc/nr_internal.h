@@ -88,9 +88,10 @@ cudaError_t launch_mixed(int mode, int nmax, int grid, const KernelArgs &a, cons
                          cudaStream_t st);
 bool mixed_bucket_ok(int mode, int nmax);
 
-// ---- paired gradient kernel (nr_pair.cu): two evaluations per thread ----
-// Used by launch_mixed / mixed_occupancy / mixed_tile_q for the 1- and
-// 2-layer gradient buckets when K >= 3.
+// ---- paired kernel (nr_pair.cu): two evaluations per thread ----
+// Used by launch_mixed / mixed_occupancy / mixed_tile_q when K >= 3 for the
+// 1- and 2-layer gradient buckets and the 1-layer forward (model, loglik)
+// bucket.
 bool pair_eligible(int mode, int nmax, int K);
 int pair_block_threads();
 cudaError_t pair_occupancy(int mode, int nmax, int K, int *blocks_per_sm);

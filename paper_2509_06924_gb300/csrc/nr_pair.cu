@@ -1,6 +1,6 @@
-// nr_pair.cu -- the gradient kernel of the 1- and 2-layer buckets with two
-// evaluations per thread in paired FP32 arithmetic (sm_100-family
-// add/mul/fma.rn.f32x2).
+// nr_pair.cu -- the kernels of the 1- and 2-layer gradient buckets and of
+// the 1-layer forward bucket (model, log-likelihood) with two evaluations
+// per thread in paired FP32 arithmetic (sm_100-family add/mul/fma.rn.f32x2).
 //
 // The mixed-precision gradient evaluation is bound by instruction issue, not
 // by the FP32 pipes: about 60 % of the issued instructions are FP32 adds,
@@ -16,6 +16,8 @@
 // hardware), negated operands are free as well; nothing is swapped between
 // the halves, which would cost moves.
 //
+// The forward modes run the same code up to the smearing sum (model: write
+// scale S + bkg; log-likelihood: the residual terms) and no adjoint.
 // Everything else follows the one-evaluation-per-thread kernel (nr_mixed.cu)
 // step for step, with the same double-float guards, the same stored
 // intermediates (1-2 layers keep all of them in registers) and the same
@@ -41,6 +43,10 @@
 #endif
 #ifndef NR_PAIR_MINB2
 #define NR_PAIR_MINB2 3
+#endif
+// CTAs per SM of the 1-layer forward (model / loglik) kernels
+#ifndef NR_PAIR_MINB_FWD
+#define NR_PAIR_MINB_FWD 8
 #endif
 // 0: the 1- and 2-layer gradient buckets keep the one-evaluation kernel
 #ifndef NR_PAIR
@@ -218,10 +224,14 @@ __device__ __forceinline__ c2 mobius2(c2 r, c2 Y, c2 &D)
 
 // ---------------------------------------------------------------- kernel --
 template <int MODE, int NMAX, int KC>
-__global__ void __launch_bounds__(kPairBlock, NMAX == 1 ? NR_PAIR_MINB1 : NR_PAIR_MINB2)
+__global__ void __launch_bounds__(kPairBlock, (MODE == kGrad || MODE == kGradRes)
+                                                  ? (NMAX == 1 ? NR_PAIR_MINB1 : NR_PAIR_MINB2)
+                                                  : NR_PAIR_MINB_FWD)
 nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
 {
-    static_assert((MODE == kGrad || MODE == kGradRes) && NMAX >= 1 && NMAX <= 2, "paired kernel: gradient modes, 1-2 layers");
+    constexpr bool GRAD = MODE == kGrad || MODE == kGradRes;
+    constexpr bool LIK = MODE != kModel;
+    static_assert(GRAD ? (NMAX >= 1 && NMAX <= 2) : NMAX == 1, "paired kernel: 1-2 layer gradients, 1-layer forward");
     constexpr int NM = NMAX;
     constexpr int BLOCK = kPairBlock;
     constexpr int WARPS = BLOCK / 32;
@@ -238,14 +248,14 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
     __shared__ StackSmem<NM> sm;
     __shared__ __align__(16) float sh_wR[2][4 * BLOCK]; // w_k R per (Q slot, node), double-buffered
     __shared__ float4 sh_qd[CAPQ];                      // (Q/2, dQ/2, R_obs, 1/err) per staged Q point
-    __shared__ float2 sh_rs[CAPQ];                      // (residual, S) per staged Q point
+    __shared__ float2 sh_rs[LIK ? CAPQ : 1];            // (residual, S) per staged Q point
     __shared__ double sh_red[WARPS][32];
     __shared__ double sh_redd[WARPS][4];
     __shared__ double sh_raw[NRAW];
     __shared__ int sh_item;
     __shared__ int sh_last;
-    __shared__ float2 sh_eq[WARPS][EQF][EQ];
-    __shared__ int sh_eqj[WARPS][EQ];
+    __shared__ float2 sh_eq[GRAD ? WARPS : 1][EQF][GRAD ? EQ : 1];
+    __shared__ int sh_eqj[GRAD ? WARPS : 1][GRAD ? EQ : 1];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -343,16 +353,20 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
         const int span = (CAPQ / TQ) * TQ;
         int sb = wi.q_lo, s_next = wi.q_lo, s_cnt = 0;
         auto consume = [&](int i) __attribute__((always_inline)) {
-            const float2 rs = sh_rs[i];
-            const float Re = __ldg(rep + sb + i);
-            if (!(Re > 0.f)) atomicOr(ka.status, NR_FLAG_BAD_ERR);
-            float t1, t2;
-            two_sum(ll_hi, fmaf(rs.x, rs.x, kLog2Pi + 2.f * logf(Re)), t1, t2);
-            ll_hi = t1;
-            ll_lo += t2;
-            const float dldm = -(rs.x * fabsf(sh_qd[i].w));
-            gsc_acc = fmaf(dldm, rs.y, gsc_acc);
-            gbk_acc += dldm;
+            if constexpr (LIK) {
+                const float2 rs = sh_rs[i];
+                const float Re = __ldg(rep + sb + i);
+                if (!(Re > 0.f)) atomicOr(ka.status, NR_FLAG_BAD_ERR);
+                float t1, t2;
+                two_sum(ll_hi, fmaf(rs.x, rs.x, kLog2Pi + 2.f * logf(Re)), t1, t2);
+                ll_hi = t1;
+                ll_lo += t2;
+                if constexpr (GRAD) {
+                    const float dldm = -(rs.x * fabsf(sh_qd[i].w));
+                    gsc_acc = fmaf(dldm, rs.y, gsc_acc);
+                    gbk_acc += dldm;
+                }
+            }
         };
         auto restage = [&](int q0) {
             __syncthreads(); // the previous super-tile's reads and pairs are complete
@@ -363,20 +377,24 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                 if (qa < wi.q_hi) {
                     v.x = 0.5f * __ldg(qp + qa);
                     v.y = 0.5f * __ldg(dqp + qa);
-                    v.z = __ldg(rop + qa);
-                    v.w = rcp_approx(__ldg(rep + qa));
-                    // may a node of this Q point reach an interior-edge band?
-                    // (negative 1/err: yes)
-                    const float a = fabsf(v.y) * g_max;
-                    const float lo = fmaxf(v.x - a, 0.f), hi = v.x + a;
-                    const float k2lo = lo * lo * (1.f - 1.5f * kEdgeFrac);
-                    const float k2hi = hi * hi * (1.f + 1.5f * kEdgeFrac);
-                    bool e = false;
-                    for (int j = 1; j <= n; ++j) {
-                        const float c = sm.med[j].x;
-                        e |= c > 0.f && c < k2hi && c > k2lo;
+                    if constexpr (LIK) {
+                        v.z = __ldg(rop + qa);
+                        v.w = rcp_approx(__ldg(rep + qa));
                     }
-                    if (e && v.w > 0.f) v.w = -v.w;
+                    if constexpr (GRAD) {
+                        // may a node of this Q point reach an interior-edge
+                        // band?  (negative 1/err: yes)
+                        const float a = fabsf(v.y) * g_max;
+                        const float lo = fmaxf(v.x - a, 0.f), hi = v.x + a;
+                        const float k2lo = lo * lo * (1.f - 1.5f * kEdgeFrac);
+                        const float k2hi = hi * hi * (1.f + 1.5f * kEdgeFrac);
+                        bool e = false;
+                        for (int j = 1; j <= n; ++j) {
+                            const float c = sm.med[j].x;
+                            e |= c > 0.f && c < k2hi && c > k2lo;
+                        }
+                        if (e && v.w > 0.f) v.w = -v.w;
+                    }
                 }
                 sh_qd[i] = v;
             }
@@ -492,215 +510,230 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                 S.x = __shfl_sync(kFull, ps, ((qslot[0] - qs0) * sgl) & 31);
                 S.y = __shfl_sync(kFull, ps, ((qslot[1] - qs0) * sgl) & 31);
             }
-            const f2 ie = make_float2(fabsf(qd[0].w), fabsf(qd[1].w));
-            const f2 res = pmul(psub(pfma(bc(scale), S, bc(bkg)), make_float2(qd[0].z, qd[1].z)), ie);
+            if constexpr (MODE == kModel) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
-                if (act[h] && kn[h] == 0) sh_rs[si_q[h]] = make_float2(half(res, h), half(S, h));
-            const f2 Rb = pmul(wks, pneg(pmul(res, ie))); // w_k scale dl/dm (0 on idle slots)
+                for (int h = 0; h < 2; ++h)
+                    if (act[h] && kn[h] == 0) ka.r_out[si.out_off + qi[h]] = fmaf(scale, half(S, h), bkg);
+            } else {
+                const f2 ie = make_float2(fabsf(qd[0].w), fabsf(qd[1].w));
+                const f2 res = pmul(psub(pfma(bc(scale), S, bc(bkg)), make_float2(qd[0].z, qd[1].z)), ie);
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    if (act[h] && kn[h] == 0) sh_rs[si_q[h]] = make_float2(half(res, h), half(S, h));
+                if constexpr (GRAD) {
+                    const f2 Rb = pmul(wks, pneg(pmul(res, ie))); // w_k scale dl/dm (0 on idle slots)
 
-            // a7: adjoint sweep from the fronting down to the backing
-            c2 Xb = c2{pmul(Xr[0].re, padd(Rb, Rb)), pmul(Xr[0].im, padd(Rb, Rb))};
-            c2 kbar = czero();
-            Kz2 kj = Kz2{k0h, bc(0.f), k0l};
-            c2 Xb_up = czero();
-            Kz2 kjm1 = kj;
-            const f2 edge_u = pmul(bc(kEdgeFrac), pmul(k0h, k0h));
-            const f2 wres = RES ? pmul(dQh, g_hi) : bc(0.f);
-            f2 res_sum = bc(0.f), res_k0 = bc(0.f);
-            auto adj_step = [&](int j, auto EDG) __attribute__((always_inline)) {
-                const bool top = j == 0, bot = j == n;
-                const float4 Ij = sm.itf[j];
-                const float4 Lj1 = sm.lay[j + 1];
-                const c2 Xb_in = Xb;
-                c2 Zj = czero();
-                const Kz2 kj1 = kst[j + 1];
-                const c2 rj = rst[j], Gj = Gst[j];
-                c2 kbar1 = czero();
-                c2 rb;
-                if (!bot) {
-                    const c2 Ej1 = Est[j + 1], Dj = Dst[j], Y = Yst[j];
-                    Zj = Y;
-                    const c2 V = cmulc2(Dj, cmulc2(Dj, Xb));
-                    rb = cmulc2(one_minus_sq2(Y), V);
-                    const c2 Yb = cmulc2(one_minus_sq2(rj), V);
-                    Xb = cmulc2(Ej1, Yb);
-                    const c2 U = cmulc2(Y, Yb);
-                    acc_fma2(oD + j, kj1.re, U.im, pneg(kj1.im), U.re);
-                    kbar1 = c2{pmul(bc(Lj1.x), U.im), pneg(pmul(bc(Lj1.x), U.re))};
-                } else {
-                    rb = Xb;
-                }
-                const c2 rr = cmulc2(rb, rj);
-                const c2 gg = cmulc2(Gj, rb);
-                const c2 sr = c2{pmul(bc(Ij.z), rr.re), pneg(pmul(bc(Ij.z), rr.im))};
-                const c2 Hm = c2{pfma(bc(-2.f), gg.re, sr.re), pfma(bc(-2.f), gg.im, sr.im)}; // conj(M) rbar
-                c2 kkj;
-                if (top) {
-                    kbar1 = c2{pfma(kj.re, Hm.re, kbar1.re), pfma(kj.re, Hm.im, kbar1.im)};
-                    kkj = c2{pmul(kj.re, kj1.re), pmul(kj.re, kj1.im)};
-                } else {
-                    kbar1 = cfmac2(kc2(kj), Hm, kbar1);
-                    kkj = cmul2(kc2(kj), kc2(kj1));
-                }
-                acc_fma2(oS + j, rr.re, kkj.re, pneg(rr.im), kkj.im);
-                const c2 Hp = c2{pfma(bc(2.f), gg.re, sr.re), pfma(bc(2.f), gg.im, sr.im)}; // conj(P) rbar
-                if (RES && top) res_k0 = pfma(kj1.re, Hp.re, pmul(kj1.im, Hp.im));
-                if (!top) {
-                    kbar = cfmac2(kc2(kj1), Hp, kbar);
-                    // k_j complete: accumulate conj(kbar) / k_j, or queue the
-                    // interior-edge evaluation
-                    const f2 m2 = pfma(kj.re, kj.re, pmul(kj.im, kj.im));
-                    b2 edge{false, false};
-                    if constexpr (decltype(EDG)::value) {
-                        edge = b2{act[0] && m2.x < edge_u.x, act[1] && m2.y < edge_u.y};
+                    // a7: adjoint sweep from the fronting down to the backing
+                    c2 Xb = c2{pmul(Xr[0].re, padd(Rb, Rb)), pmul(Xr[0].im, padd(Rb, Rb))};
+                    c2 kbar = czero();
+                    Kz2 kj = Kz2{k0h, bc(0.f), k0l};
+                    c2 Xb_up = czero();
+                    Kz2 kjm1 = kj;
+                    const f2 edge_u = pmul(bc(kEdgeFrac), pmul(k0h, k0h));
+                    const f2 wres = RES ? pmul(dQh, g_hi) : bc(0.f);
+                    f2 res_sum = bc(0.f), res_k0 = bc(0.f);
+                    auto adj_step = [&](int j, auto EDG) __attribute__((always_inline)) {
+                        const bool top = j == 0, bot = j == n;
+                        const float4 Ij = sm.itf[j];
+                        const float4 Lj1 = sm.lay[j + 1];
+                        const c2 Xb_in = Xb;
+                        c2 Zj = czero();
+                        const Kz2 kj1 = kst[j + 1];
+                        const c2 rj = rst[j], Gj = Gst[j];
+                        c2 kbar1 = czero();
+                        c2 rb;
+                        if (!bot) {
+                            const c2 Ej1 = Est[j + 1], Dj = Dst[j], Y = Yst[j];
+                            Zj = Y;
+                            const c2 V = cmulc2(Dj, cmulc2(Dj, Xb));
+                            rb = cmulc2(one_minus_sq2(Y), V);
+                            const c2 Yb = cmulc2(one_minus_sq2(rj), V);
+                            Xb = cmulc2(Ej1, Yb);
+                            const c2 U = cmulc2(Y, Yb);
+                            acc_fma2(oD + j, kj1.re, U.im, pneg(kj1.im), U.re);
+                            kbar1 = c2{pmul(bc(Lj1.x), U.im), pneg(pmul(bc(Lj1.x), U.re))};
+                        } else {
+                            rb = Xb;
+                        }
+                        const c2 rr = cmulc2(rb, rj);
+                        const c2 gg = cmulc2(Gj, rb);
+                        const c2 sr = c2{pmul(bc(Ij.z), rr.re), pneg(pmul(bc(Ij.z), rr.im))};
+                        const c2 Hm = c2{pfma(bc(-2.f), gg.re, sr.re), pfma(bc(-2.f), gg.im, sr.im)}; // conj(M) rbar
+                        c2 kkj;
+                        if (top) {
+                            kbar1 = c2{pfma(kj.re, Hm.re, kbar1.re), pfma(kj.re, Hm.im, kbar1.im)};
+                            kkj = c2{pmul(kj.re, kj1.re), pmul(kj.re, kj1.im)};
+                        } else {
+                            kbar1 = cfmac2(kc2(kj), Hm, kbar1);
+                            kkj = cmul2(kc2(kj), kc2(kj1));
+                        }
+                        acc_fma2(oS + j, rr.re, kkj.re, pneg(rr.im), kkj.im);
+                        const c2 Hp = c2{pfma(bc(2.f), gg.re, sr.re), pfma(bc(2.f), gg.im, sr.im)}; // conj(P) rbar
+                        if (RES && top) res_k0 = pfma(kj1.re, Hp.re, pmul(kj1.im, Hp.im));
+                        if (!top) {
+                            kbar = cfmac2(kc2(kj1), Hp, kbar);
+                            // k_j complete: accumulate conj(kbar) / k_j, or queue the
+                            // interior-edge evaluation
+                            const f2 m2 = pfma(kj.re, kj.re, pmul(kj.im, kj.im));
+                            b2 edge{false, false};
+                            if constexpr (decltype(EDG)::value) {
+                                edge = b2{act[0] && m2.x < edge_u.x, act[1] && m2.y < edge_u.y};
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const bool eh = h ? edge.y : edge.x;
-                            const unsigned em = __ballot_sync(kFull, eh);
-                            if (em) {
-                                if (eh) {
-                                    const int slot = eq_cnt + __popc(em & ((1u << lane) - 1u));
-                                    if constexpr (RES)
-                                        sh_eq[warp][EQF - 1][slot] = make_float2(half(k0h, h) * half(wres, h), 0.f);
-                                    sh_eq[warp][0][slot] = make_float2(half(kjm1.re, h), half(kjm1.im, h));
-                                    sh_eq[warp][1][slot] = make_float2(half(kj.re, h), half(kj.im, h));
-                                    sh_eq[warp][2][slot] = make_float2(half(kj1.re, h), half(kj1.im, h));
-                                    sh_eq[warp][3][slot] = make_float2(half(Zj.re, h), half(Zj.im, h));
-                                    sh_eq[warp][4][slot] = make_float2(half(Xb_up.re, h), half(Xb_up.im, h));
-                                    sh_eqj[warp][slot] = j;
+                                for (int h = 0; h < 2; ++h) {
+                                    const bool eh = h ? edge.y : edge.x;
+                                    const unsigned em = __ballot_sync(kFull, eh);
+                                    if (em) {
+                                        if (eh) {
+                                            const int slot = eq_cnt + __popc(em & ((1u << lane) - 1u));
+                                            if constexpr (RES)
+                                                sh_eq[warp][EQF - 1][slot] = make_float2(half(k0h, h) * half(wres, h), 0.f);
+                                            sh_eq[warp][0][slot] = make_float2(half(kjm1.re, h), half(kjm1.im, h));
+                                            sh_eq[warp][1][slot] = make_float2(half(kj.re, h), half(kj.im, h));
+                                            sh_eq[warp][2][slot] = make_float2(half(kj1.re, h), half(kj1.im, h));
+                                            sh_eq[warp][3][slot] = make_float2(half(Zj.re, h), half(Zj.im, h));
+                                            sh_eq[warp][4][slot] = make_float2(half(Xb_up.re, h), half(Xb_up.im, h));
+                                            sh_eqj[warp][slot] = j;
+                                        }
+                                        eq_cnt += __popc(em);
+                                    }
                                 }
-                                eq_cnt += __popc(em);
+                            }
+                            const c2 kq = cmul2(kbar, kc2(kj));
+                            f2 inv = prcp(pmax(m2, bc(1e-30f)));
+                            if constexpr (decltype(EDG)::value) inv = psel(edge, bc(0.f), inv);
+                            const f2 ur = pmul(kq.re, inv), ui = pneg(pmul(kq.im, inv));
+                            accr[oUr + j - 1] = padd(accr[oUr + j - 1], ur);
+                            accr[oUi + j - 1] = padd(accr[oUi + j - 1], ui);
+                            if constexpr (RES) res_sum = padd(res_sum, ur);
+                        }
+                        Xb_up = Xb_in;
+                        kbar = kbar1;
+                        kjm1 = kj;
+                        kj = kj1;
+                        if (bot) { // backing medium n+1
+                            const c2 kk = cmul2(kbar, kc2(kj));
+                            const f2 m2 = pfma(kj.re, kj.re, pmul(kj.im, kj.im));
+                            const f2 inv = prcp(pmax(m2, bc(1e-30f)));
+                            const f2 ur = pmul(kk.re, inv), ui = pneg(pmul(kk.im, inv));
+                            accr[oUr + j] = padd(accr[oUr + j], ur);
+                            accr[oUi + j] = padd(accr[oUi + j], ui);
+                            if constexpr (RES) res_sum = padd(res_sum, ur);
+                        }
+                    };
+                    auto sweep = [&](auto EDG) __attribute__((always_inline)) {
+#pragma unroll
+                        for (int j = 0; j <= NM; ++j)
+                            if (j <= n) adj_step(j, EDG);
+                        if constexpr (decltype(EDG)::value) {
+                            while (eq_cnt >= 32) {
+                                __syncwarp();
+                                eq_drain(32);
                             }
                         }
-                    }
-                    const c2 kq = cmul2(kbar, kc2(kj));
-                    f2 inv = prcp(pmax(m2, bc(1e-30f)));
-                    if constexpr (decltype(EDG)::value) inv = psel(edge, bc(0.f), inv);
-                    const f2 ur = pmul(kq.re, inv), ui = pneg(pmul(kq.im, inv));
-                    accr[oUr + j - 1] = padd(accr[oUr + j - 1], ur);
-                    accr[oUi + j - 1] = padd(accr[oUi + j - 1], ui);
-                    if constexpr (RES) res_sum = padd(res_sum, ur);
-                }
-                Xb_up = Xb_in;
-                kbar = kbar1;
-                kjm1 = kj;
-                kj = kj1;
-                if (bot) { // backing medium n+1
-                    const c2 kk = cmul2(kbar, kc2(kj));
-                    const f2 m2 = pfma(kj.re, kj.re, pmul(kj.im, kj.im));
-                    const f2 inv = prcp(pmax(m2, bc(1e-30f)));
-                    const f2 ur = pmul(kk.re, inv), ui = pneg(pmul(kk.im, inv));
-                    accr[oUr + j] = padd(accr[oUr + j], ur);
-                    accr[oUi + j] = padd(accr[oUi + j], ui);
-                    if constexpr (RES) res_sum = padd(res_sum, ur);
-                }
-            };
-            auto sweep = [&](auto EDG) __attribute__((always_inline)) {
-#pragma unroll
-                for (int j = 0; j <= NM; ++j)
-                    if (j <= n) adj_step(j, EDG);
-                if constexpr (decltype(EDG)::value) {
-                    while (eq_cnt >= 32) {
-                        __syncwarp();
-                        eq_drain(32);
-                    }
-                }
-            };
-            // the staged sign of 1/err marks Q points whose nodes may reach an
-            // interior-edge band (warp-uniform choice)
-            if (__any_sync(kFull, (act[0] && qd[0].w < 0.f) || (act[1] && qd[1].w < 0.f)))
-                sweep(std::true_type{});
-            else
-                sweep(std::false_type{});
-            if constexpr (RES) gres_acc = pfma(wres, pfma(k0h, res_sum, res_k0), gres_acc);
+                    };
+                    // the staged sign of 1/err marks Q points whose nodes may reach an
+                    // interior-edge band (warp-uniform choice)
+                    if (__any_sync(kFull, (act[0] && qd[0].w < 0.f) || (act[1] && qd[1].w < 0.f)))
+                        sweep(std::true_type{});
+                    else
+                        sweep(std::false_type{});
+                    if constexpr (RES) gres_acc = pfma(wres, pfma(k0h, res_sum, res_k0), gres_acc);
+                } // GRAD
+            } // LIK
         }
 
-        if (eq_cnt > 0) {
-            __syncwarp();
-            eq_drain(eq_cnt);
-        }
-        // ---- CTA reduction of the item's partial sums into sh_raw ----
-        __syncthreads();
-        for (int i = tid; i < s_cnt; i += BLOCK) consume(i);
-        static_assert(NACC <= 32, "register partials exceed one reduction batch");
-#pragma unroll
-        for (int t = 0; t < NACC; ++t) {
-            float v = accr[t].x + accr[t].y;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-            if (lane == 0) sh_red[warp][t] = (double)v;
-        }
-        __syncthreads();
-        if (tid < NACC) {
-            const int t = tid;
-            // accumulator slot -> raw index for this stack's n (-1: unused)
-            const int i = t < NM ? (t < n ? t : -1)
-                          : t < 2 * NM + 1 ? (t - NM <= n ? n + (t - NM) : -1)
-                          : t < 3 * NM + 2 ? (t - 2 * NM - 1 <= n ? 2 * n + 1 + (t - 2 * NM - 1) : -1)
-                                           : (t - 3 * NM - 2 <= n ? 3 * n + 2 + (t - 3 * NM - 2) : -1);
-            if (i >= 0) {
-                double s = 0.0;
-                for (int w = 0; w < WARPS; ++w) s += sh_red[w][t];
-                sh_raw[i] = s;
+        if constexpr (LIK) {
+            if constexpr (GRAD) {
+                if (eq_cnt > 0) {
+                    __syncwarp();
+                    eq_drain(eq_cnt);
+                }
             }
-        }
-        __syncthreads();
-        {   // loglik (float pair), d/dscale, d/dbkg, d/d ln(dQ scale)
-            float h = ll_hi, l = ll_lo, a1 = gsc_acc, a2 = gbk_acc, a3 = gres_acc.x + gres_acc.y;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float h2 = __shfl_xor_sync(kFull, h, o), l2 = __shfl_xor_sync(kFull, l, o);
-                float s, e;
-                two_sum(h, h2, s, e);
-                h = s;
-                l = __fadd_rn(__fadd_rn(l, l2), e);
-                a1 += __shfl_xor_sync(kFull, a1, o);
-                a2 += __shfl_xor_sync(kFull, a2, o);
-                if constexpr (RES) a3 += __shfl_xor_sync(kFull, a3, o);
-            }
-            if (lane == 0) {
-                sh_redd[warp][0] = (double)h + (double)l;
-                sh_redd[warp][1] = a1;
-                sh_redd[warp][2] = a2;
-                sh_redd[warp][3] = a3;
-            }
-        }
-        __syncthreads();
-        if (tid < (RES ? 4 : 3)) {
-            double s = 0.0;
-            for (int w = 0; w < WARPS; ++w) s += sh_redd[w][tid];
-            sh_raw[4 * n + 3 + tid] = s;
-        }
-        __syncthreads();
-        const int nout = 4 * n + (RES ? 7 : 6);
-        if (si.n_chunks == 1) {
-            finalize_stack<MODE>(sh_raw, n, p, wi.stack, si.par_off, ka.ll_out, ka.grad_out, ka.res_out, tid,
-                                 BLOCK);
-        } else {
-            double *slot = ka.partials + si.part_base + (int64_t)wi.chunk * n_slot(n);
-            for (int i = tid; i < nout; i += BLOCK) slot[i] = sh_raw[i];
-            __threadfence();
+            // ---- CTA reduction of the item's partial sums into sh_raw ----
             __syncthreads();
-            if (tid == 0) {
-                const int prev = atomicAdd(&ka.stack_done[wi.stack], 1);
-                sh_last = prev == si.n_chunks - 1;
-            }
-            __syncthreads();
-            if (sh_last) {
-                __threadfence();
-                for (int i = tid; i < nout; i += BLOCK) {
-                    double s = 0.0;
-                    for (int c = 0; c < si.n_chunks; ++c)
-                        s += __ldcg(ka.partials + si.part_base + (int64_t)c * n_slot(n) + i);
-                    sh_raw[i] = s;
+            for (int i = tid; i < s_cnt; i += BLOCK) consume(i);
+            static_assert(NACC <= 32, "register partials exceed one reduction batch");
+            if constexpr (GRAD) {
+#pragma unroll
+                for (int t = 0; t < NACC; ++t) {
+                    float v = accr[t].x + accr[t].y;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+                    if (lane == 0) sh_red[warp][t] = (double)v;
                 }
                 __syncthreads();
-                finalize_stack<MODE>(sh_raw, n, p, wi.stack, si.par_off, ka.ll_out, ka.grad_out, ka.res_out,
-                                     tid, BLOCK);
-                if (tid == 0) ka.stack_done[wi.stack] = 0;
+                if (tid < NACC) {
+                    const int t = tid;
+                    // accumulator slot -> raw index for this stack's n (-1: unused)
+                    const int i = t < NM ? (t < n ? t : -1)
+                                  : t < 2 * NM + 1 ? (t - NM <= n ? n + (t - NM) : -1)
+                                  : t < 3 * NM + 2 ? (t - 2 * NM - 1 <= n ? 2 * n + 1 + (t - 2 * NM - 1) : -1)
+                                                   : (t - 3 * NM - 2 <= n ? 3 * n + 2 + (t - 3 * NM - 2) : -1);
+                    if (i >= 0) {
+                        double s = 0.0;
+                        for (int w = 0; w < WARPS; ++w) s += sh_red[w][t];
+                        sh_raw[i] = s;
+                    }
+                }
+                __syncthreads();
+            } // GRAD
+            {   // loglik (float pair), d/dscale, d/dbkg, d/d ln(dQ scale)
+                float h = ll_hi, l = ll_lo, a1 = gsc_acc, a2 = gbk_acc, a3 = gres_acc.x + gres_acc.y;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float h2 = __shfl_xor_sync(kFull, h, o), l2 = __shfl_xor_sync(kFull, l, o);
+                    float s, e;
+                    two_sum(h, h2, s, e);
+                    h = s;
+                    l = __fadd_rn(__fadd_rn(l, l2), e);
+                    a1 += __shfl_xor_sync(kFull, a1, o);
+                    a2 += __shfl_xor_sync(kFull, a2, o);
+                    if constexpr (RES) a3 += __shfl_xor_sync(kFull, a3, o);
+                }
+                if (lane == 0) {
+                    sh_redd[warp][0] = (double)h + (double)l;
+                    sh_redd[warp][1] = a1;
+                    sh_redd[warp][2] = a2;
+                    sh_redd[warp][3] = a3;
+                }
             }
-        }
+            __syncthreads();
+            if (tid < (RES ? 4 : 3)) {
+                double s = 0.0;
+                for (int w = 0; w < WARPS; ++w) s += sh_redd[w][tid];
+                sh_raw[4 * n + 3 + tid] = s;
+            }
+            __syncthreads();
+            const int nout = GRAD ? 4 * n + (RES ? 7 : 6) : 1;
+            const int off0 = GRAD ? 0 : 4 * n + 3; // loglik mode: llsum only
+            if (si.n_chunks == 1) {
+                finalize_stack<MODE>(sh_raw, n, p, wi.stack, si.par_off, ka.ll_out, ka.grad_out, ka.res_out, tid,
+                                     BLOCK);
+            } else {
+                double *slot = ka.partials + si.part_base + (int64_t)wi.chunk * n_slot(n);
+                for (int i = tid; i < nout; i += BLOCK) slot[off0 + i] = sh_raw[off0 + i];
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) {
+                    const int prev = atomicAdd(&ka.stack_done[wi.stack], 1);
+                    sh_last = prev == si.n_chunks - 1;
+                }
+                __syncthreads();
+                if (sh_last) {
+                    __threadfence();
+                    for (int i = tid; i < nout; i += BLOCK) {
+                        double s = 0.0;
+                        for (int c = 0; c < si.n_chunks; ++c)
+                            s += __ldcg(ka.partials + si.part_base + (int64_t)c * n_slot(n) + off0 + i);
+                        sh_raw[off0 + i] = s;
+                    }
+                    __syncthreads();
+                    finalize_stack<MODE>(sh_raw, n, p, wi.stack, si.par_off, ka.ll_out, ka.grad_out, ka.res_out,
+                                         tid, BLOCK);
+                    if (tid == 0) ka.stack_done[wi.stack] = 0;
+                }
+            }
+        } // LIK
         __syncthreads(); // sm / sh_raw / sh_item / sh_wR reused by the next item
     }
     // last CTA out resets the queue for the next launch
@@ -754,13 +787,15 @@ cudaError_t pair_occupancy_one(int K, int *blocks)
 
 bool pair_eligible(int mode, int nmax, int K)
 {
-    return NR_PAIR && is_grad_mode(mode) && (nmax == 1 || nmax == 2) && K >= 3;
+    return NR_PAIR && K >= 3 && (is_grad_mode(mode) ? (nmax == 1 || nmax == 2) : nmax == 1);
 }
 
 int pair_block_threads() { return kPairBlock; }
 
 cudaError_t pair_occupancy(int mode, int nmax, int K, int *blocks)
 {
+    if (mode == kModel) return pair_occupancy_one<kModel, 1>(K, blocks);
+    if (mode == kLoglik) return pair_occupancy_one<kLoglik, 1>(K, blocks);
     if (mode == kGradRes) return nmax == 1 ? pair_occupancy_one<kGradRes, 1>(K, blocks)
                                            : pair_occupancy_one<kGradRes, 2>(K, blocks);
     return nmax == 1 ? pair_occupancy_one<kGrad, 1>(K, blocks) : pair_occupancy_one<kGrad, 2>(K, blocks);
@@ -768,6 +803,8 @@ cudaError_t pair_occupancy(int mode, int nmax, int K, int *blocks)
 
 cudaError_t launch_pair(int mode, int nmax, int grid, const KernelArgs &a, const QuadConst &qc, cudaStream_t st)
 {
+    if (mode == kModel) return pair_launch_one<kModel, 1>(grid, a, qc, st);
+    if (mode == kLoglik) return pair_launch_one<kLoglik, 1>(grid, a, qc, st);
     if (mode == kGradRes) return nmax == 1 ? pair_launch_one<kGradRes, 1>(grid, a, qc, st)
                                            : pair_launch_one<kGradRes, 2>(grid, a, qc, st);
     return nmax == 1 ? pair_launch_one<kGrad, 1>(grid, a, qc, st) : pair_launch_one<kGrad, 2>(grid, a, qc, st);
