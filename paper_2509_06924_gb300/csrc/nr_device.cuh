@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "nr_internal.h"
 
@@ -38,6 +39,18 @@ constexpr float kEdgeFrac = NR_EDGE_FRAC;
 #ifndef NR_EXACT1
 #define NR_EXACT1 1
 #endif
+
+// Position of a sweep step, known at compile time or tested at run time: the
+// rolled sweeps peel their first and last steps so that the steps between
+// them carry no branches on j.
+enum : int { kNo = 0, kYes = 1, kRt = 2 };
+template <int V>
+using Pos = std::integral_constant<int, V>;
+template <class P>
+__device__ __forceinline__ bool pos_flag(P, bool rt)
+{
+    return P::value == kRt ? rt : P::value == kYes;
+}
 
 // ------------------------------------------------------------ primitives --
 __device__ __forceinline__ float rcp_approx(float x)
@@ -349,6 +362,27 @@ __device__ __forceinline__ float2 edge_entry_ubar(float2 node, float2 Z, float2 
     const Kz kj = medium_kz<true>(p_hi, p_lo, med[j]);
     const Kz kb = j == n ? medium_kz<false>(p_hi, p_lo, med[j + 1]) : medium_kz<true>(p_hi, p_lo, med[j + 1]);
     return edge_ubar(kc(ka), kc(kj), kc(kb), lay[j - 1].w, lay[j].w, 0.5f * lay[j].x, Z, j == n, Xbu);
+}
+
+// Drains `cnt` queued interior-edge entries of one warp (one per lane) into
+// per-thread partials kept in shared memory (acc points at this thread's
+// slot of medium 1's Re-accumulator; stride between accumulators `stride`,
+// Re -> Im distance `im_off`; med, lay: the staged stack entries).  Kept out
+// of line so that the rolled sweep it is called from keeps its register budget.
+template <int EQ, bool RES>
+__device__ __noinline__ float eq_drain_smem(float2 (*q)[EQ], const int *qj, const float4 *med, const float4 *lay,
+                                            int n, int lane, int cnt, float *acc, int stride, int im_off)
+{
+    float res = 0.f; // the resolution-mode term of the entry (factor in q[3])
+    if (lane < cnt) {
+        const int j = qj[lane];
+        const float2 ub = edge_entry_ubar(q[0][lane], q[1][lane], q[2][lane], j, n, med, lay);
+        // conj(kbar)/k_j = 2 conj(ubar)
+        acc[(j - 1) * stride] += 2.f * ub.x;
+        acc[(j - 1) * stride + im_off] += -2.f * ub.y;
+        if constexpr (RES) res = 2.f * ub.x * q[3][lane].x;
+    }
+    return res;
 }
 
 // Per-stack parameters staged in shared memory, one 16-byte entry per

@@ -44,6 +44,17 @@
 #ifndef NR_PAIR_MINB2
 #define NR_PAIR_MINB2 3
 #endif
+// CTAs per SM asked of the rolled (>= 3 layer) gradient kernels; their
+// shared-memory partials and X_j usually set the occupancy first
+#ifndef NR_PAIR_MINB_DEEP
+#define NR_PAIR_MINB_DEEP 3
+#endif
+// gradient buckets [NR_PAIR_DEEP_FROM, 20] run the rolled paired kernel
+// (NR_PAIR_DEEP_FROM 0: none); deeper buckets keep the one-evaluation kernel,
+// whose shared-memory state per evaluation is half as large
+#ifndef NR_PAIR_DEEP_FROM
+#define NR_PAIR_DEEP_FROM 4
+#endif
 // CTAs per SM of the 1-layer forward (model / loglik) kernels
 #ifndef NR_PAIR_MINB_FWD
 #define NR_PAIR_MINB_FWD 8
@@ -57,6 +68,10 @@ namespace nrimpl {
 namespace {
 
 constexpr int kPairBlock = NR_PAIR_BLOCK;
+#ifndef NR_PAIR_DEEP_UNROLL
+#define NR_PAIR_DEEP_UNROLL 1
+#endif
+constexpr int kPairDeepUnroll = NR_PAIR_DEEP_UNROLL; // unroll of the rolled sweeps
 
 // ---------------------------------------------------- paired FP32 values --
 // f2 holds one FP32 value of each of the thread's two evaluations.
@@ -222,27 +237,47 @@ __device__ __forceinline__ c2 mobius2(c2 r, c2 Y, c2 &D)
     return cmul2(cadd2(r, Y), D);
 }
 
+// ---------------------------------------------------------------- traits --
+// STORE (1-2 layer gradients): unrolled sweeps, every forward intermediate
+// and the partial gradients in registers.  ROLL (3-64 layers): rolled sweeps
+// peeled at the first and last steps; X_j (both halves) and the partial
+// gradients (both halves summed, one float per thread) in shared memory;
+// k, r and E recomputed in the adjoint; edge entries keep the node k_0.
+template <int MODE, int NMAX>
+struct PairTraits {
+    static constexpr bool GRAD = MODE == kGrad || MODE == kGradRes;
+    static constexpr bool ROLL = GRAD && NMAX > 2;
+    static constexpr int NACC = 4 * NMAX + 3;
+    static constexpr int MINB = !GRAD ? NR_PAIR_MINB_FWD : NMAX == 1 ? NR_PAIR_MINB1
+                                : NMAX == 2 ? NR_PAIR_MINB2 : NR_PAIR_MINB_DEEP;
+    static constexpr size_t DYN = ROLL ? (size_t)NACC * kPairBlock * 4 + (size_t)(NMAX + 1) * kPairBlock * 16 : 0;
+};
+
 // ---------------------------------------------------------------- kernel --
 template <int MODE, int NMAX, int KC>
-__global__ void __launch_bounds__(kPairBlock, (MODE == kGrad || MODE == kGradRes)
-                                                  ? (NMAX == 1 ? NR_PAIR_MINB1 : NR_PAIR_MINB2)
-                                                  : NR_PAIR_MINB_FWD)
+__global__ void __launch_bounds__(kPairBlock, PairTraits<MODE, NMAX>::MINB)
 nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
 {
-    constexpr bool GRAD = MODE == kGrad || MODE == kGradRes;
+    using PT = PairTraits<MODE, NMAX>;
+    constexpr bool GRAD = PT::GRAD;
+    constexpr bool ROLL = PT::ROLL;
     constexpr bool LIK = MODE != kModel;
-    static_assert(GRAD ? (NMAX >= 1 && NMAX <= 2) : NMAX == 1, "paired kernel: 1-2 layer gradients, 1-layer forward");
+    static_assert(GRAD ? (NMAX >= 1 && NMAX <= NR_MAX_LAYERS) : NMAX == 1,
+                  "paired kernel: gradients of any bucket, 1-layer forward");
     constexpr int NM = NMAX;
     constexpr int BLOCK = kPairBlock;
     constexpr int WARPS = BLOCK / 32;
     constexpr bool RES = MODE == kGradRes;
-    constexpr int NACC = 4 * NM + 3;
+    constexpr int NACC = PT::NACC;
     constexpr int NRAW = 4 * NM + 7;
-    constexpr int CAPQ = 256;
-    // a warp's tile queues at most 64 n interior-edge entries and keeps
-    // fewer than 32 between tiles
-    constexpr int EQ = 64 * NM + 32;
-    constexpr int EQF = 5 + (RES ? 1 : 0); // k_{j-1}, k_j, k_{j+1}, Z, Xbar_{j-1} (+ k_0 dk_0/d ln f)
+    constexpr int CAPQ = ROLL ? 96 : 256;
+    // a warp's STORE tile queues at most 64 n interior-edge entries and keeps
+    // fewer than 32 between tiles; the rolled sweeps drain at 32 after each
+    // half's entries of a step
+    constexpr int EQ = ROLL ? 64 : 64 * NM + 32;
+    // STORE: k_{j-1}, k_j, k_{j+1}, Z, Xbar_{j-1}; ROLL: node k_0, Z,
+    // Xbar_{j-1}; (+ k_0 dk_0/d ln f)
+    constexpr int EQF = (ROLL ? 3 : 5) + (RES ? 1 : 0);
     static_assert(CAPQ >= 2 * BLOCK / kSubLanes, "a super-tile holds at least one tile");
 
     __shared__ StackSmem<NM> sm;
@@ -256,6 +291,10 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
     __shared__ int sh_last;
     __shared__ float2 sh_eq[GRAD ? WARPS : 1][EQF][GRAD ? EQ : 1];
     __shared__ int sh_eqj[GRAD ? WARPS : 1][GRAD ? EQ : 1];
+    // ROLL: [NACC][BLOCK] partial gradients, then [NM+1][BLOCK] X_j pairs
+    extern __shared__ __align__(16) float sh_dyn[];
+    float *sh_acc = sh_dyn;
+    float4 *sh_X = reinterpret_cast<float4 *>(sh_dyn + (ROLL ? NACC * BLOCK : 0));
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -308,19 +347,37 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
         const double *p = ka.params + si.par_off;
         stage_stack<NM>(sm, p, n, tid, ka.status);
 
-        f2 accr[NACC];
+        f2 accr[ROLL ? 1 : NACC];
+        if constexpr (ROLL) {
+            for (int i = 0; i < NACC; ++i) sh_acc[i * BLOCK + tid] = 0.f;
+        } else {
 #pragma unroll
-        for (int i = 0; i < NACC; ++i) accr[i] = bc(0.f);
+            for (int i = 0; i < NACC; ++i) accr[i] = bc(0.f);
+        }
         constexpr int oD = 0, oUr = NM, oUi = 2 * NM + 1, oS = 3 * NM + 2;
-        // accr[idx] += a b + c d
+        // partial gradient idx += v (both halves)
+        auto acc_add = [&](int idx, f2 v) __attribute__((always_inline)) {
+            if constexpr (ROLL) sh_acc[idx * BLOCK + tid] += v.x + v.y;
+            else accr[idx] = padd(accr[idx], v);
+        };
+        // partial gradient idx += a b + c d
         auto acc_fma2 = [&](int idx, f2 a, f2 b, f2 c, f2 d) __attribute__((always_inline)) {
-            accr[idx] = pfma(a, b, pfma(c, d, accr[idx]));
+            if constexpr (ROLL) {
+                const f2 t = pfma(a, b, pmul(c, d));
+                sh_acc[idx * BLOCK + tid] += t.x + t.y;
+            } else {
+                accr[idx] = pfma(a, b, pfma(c, d, accr[idx]));
+            }
         };
         f2 gres_acc = bc(0.f);
         int eq_cnt = 0; // entries in this warp's interior-edge queue (warp-uniform)
         // drain `cnt` <= 32 queued entries, one per lane (scalar edge adjoint)
         auto eq_drain = [&](int cnt) {
-            if (lane < cnt) {
+            if constexpr (ROLL) {
+                const float r = eq_drain_smem<EQ, RES>(sh_eq[warp], sh_eqj[warp], sm.med, sm.lay, n, lane, cnt,
+                                                       sh_acc + oUr * BLOCK + tid, BLOCK, (oUi - oUr) * BLOCK);
+                if constexpr (RES) gres_acc.x += r;
+            } else if (lane < cnt) {
                 const int j = sh_eqj[warp][lane];
                 const float2 ub = edge_ubar(sh_eq[warp][0][lane], sh_eq[warp][1][lane], sh_eq[warp][2][lane],
                                             sm.lay[j - 1].w, sm.lay[j].w, 0.5f * sm.lay[j].x, sh_eq[warp][3][lane],
@@ -438,15 +495,15 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
             f2 p_lo = pfma(k0h, k0h, pneg(p_hi));
             p_lo = pfma(padd(k0h, k0h), k0l, p_lo);
 
-            // a3-a6 forward from the backing up; every intermediate is kept
-            Kz2 kst[NM + 2];
-            c2 rst[NM + 1], Gst[NM + 1], Est[NM + 2], Dst[NM + 1], Yst[NM + 1], Xr[NM + 1];
+            // a3-a6 forward from the backing up (STORE keeps every
+            // intermediate; ROLL keeps X_j in shared memory)
+            Kz2 kst[ROLL ? 1 : NM + 2];
+            c2 rst[ROLL ? 1 : NM + 1], Gst[ROLL ? 1 : NM + 1], Est[ROLL ? 1 : NM + 2], Dst[ROLL ? 1 : NM + 1],
+                Yst[ROLL ? 1 : NM + 1];
             Kz2 kbelow = medium_kz2<false>(p_hi, p_lo, sm.med[n + 1]);
             c2 Xbelow = czero();
-#pragma unroll
-            for (int j = NM; j >= 0; --j) {
-                if (j > n) continue;
-                const bool top = j == 0, bot = j == n;
+            auto fwd_step = [&](int j, auto TOP, auto BOT) __attribute__((always_inline)) {
+                const bool top = pos_flag(TOP, j == 0), bot = pos_flag(BOT, j == n);
                 Kz2 kj;
                 if (top) kj = Kz2{k0h, bc(0.f), k0l};
                 else kj = medium_kz2<true>(p_hi, p_lo, sm.med[j]);
@@ -457,22 +514,37 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                 c2 Xj;
                 if (bot) {
                     Xj = rj;
-                    kst[j + 1] = kbelow;
+                    if constexpr (!ROLL) kst[j + 1] = kbelow;
                 } else {
                     const c2 Ej = layer_phase2(kbelow, sm.lay[j + 1]);
                     const c2 Yj = cmul2(Xbelow, Ej);
                     c2 Dj;
                     Xj = mobius2(rj, Yj, Dj);
-                    Est[j + 1] = Ej;
-                    Dst[j] = Dj;
-                    Yst[j] = Yj;
+                    if constexpr (!ROLL) {
+                        Est[j + 1] = Ej;
+                        Dst[j] = Dj;
+                        Yst[j] = Yj;
+                    }
                 }
-                kst[j] = kj;
-                rst[j] = rj;
-                Gst[j] = Gj;
-                Xr[j] = Xj;
+                if constexpr (ROLL) {
+                    sh_X[j * BLOCK + tid] = make_float4(Xj.re.x, Xj.re.y, Xj.im.x, Xj.im.y);
+                } else {
+                    kst[j] = kj;
+                    rst[j] = rj;
+                    Gst[j] = Gj;
+                }
                 Xbelow = Xj;
                 kbelow = kj;
+            };
+            if constexpr (ROLL) {
+                fwd_step(n, Pos<kRt>{}, Pos<kYes>{});
+#pragma unroll kPairDeepUnroll
+                for (int j = n - 1; j >= 1; --j) fwd_step(j, Pos<kNo>{}, Pos<kNo>{});
+                if (n >= 1) fwd_step(0, Pos<kYes>{}, Pos<kNo>{});
+            } else {
+#pragma unroll
+                for (int j = NM; j >= 0; --j)
+                    if (j <= n) fwd_step(j, Pos<kRt>{}, Pos<kRt>{});
             }
             f2 R = pfma(Xbelow.re, Xbelow.re, pmul(Xbelow.im, Xbelow.im));
             if (!qok.x) R.x = __int_as_float(0x7fffffff);
@@ -524,7 +596,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                     const f2 Rb = pmul(wks, pneg(pmul(res, ie))); // w_k scale dl/dm (0 on idle slots)
 
                     // a7: adjoint sweep from the fronting down to the backing
-                    c2 Xb = c2{pmul(Xr[0].re, padd(Rb, Rb)), pmul(Xr[0].im, padd(Rb, Rb))};
+                    c2 Xb = c2{pmul(Xbelow.re, padd(Rb, Rb)), pmul(Xbelow.im, padd(Rb, Rb))}; // X_0
                     c2 kbar = czero();
                     Kz2 kj = Kz2{k0h, bc(0.f), k0l};
                     c2 Xb_up = czero();
@@ -532,18 +604,42 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                     const f2 edge_u = pmul(bc(kEdgeFrac), pmul(k0h, k0h));
                     const f2 wres = RES ? pmul(dQh, g_hi) : bc(0.f);
                     f2 res_sum = bc(0.f), res_k0 = bc(0.f);
-                    auto adj_step = [&](int j, auto EDG) __attribute__((always_inline)) {
-                        const bool top = j == 0, bot = j == n;
+                    auto adj_step = [&](int j, auto TOP, auto BOT, auto EDG) __attribute__((always_inline)) {
+                        const bool top = pos_flag(TOP, j == 0), bot = pos_flag(BOT, j == n);
                         const float4 Ij = sm.itf[j];
                         const float4 Lj1 = sm.lay[j + 1];
                         const c2 Xb_in = Xb;
                         c2 Zj = czero();
-                        const Kz2 kj1 = kst[j + 1];
-                        const c2 rj = rst[j], Gj = Gst[j];
+                        Kz2 kj1;
+                        c2 rj, Gj, kkj;
+                        if constexpr (ROLL) {
+                            const float4 Mj1 = sm.med[j + 1];
+                            kj1 = bot ? medium_kz2<false>(p_hi, p_lo, Mj1) : medium_kz2<true>(p_hi, p_lo, Mj1);
+                            rj = top ? fresnel_nc2<true>(kc2(kj), kc2(kj1), Ij, Gj, kkj)
+                                     : fresnel_nc2<false>(kc2(kj), kc2(kj1), Ij, Gj, kkj);
+                        } else {
+                            kj1 = kst[j + 1];
+                            rj = rst[j];
+                            Gj = Gst[j];
+                            kkj = top ? c2{pmul(kj.re, kj1.re), pmul(kj.re, kj1.im)} : cmul2(kc2(kj), kc2(kj1));
+                        }
                         c2 kbar1 = czero();
                         c2 rb;
                         if (!bot) {
-                            const c2 Ej1 = Est[j + 1], Dj = Dst[j], Y = Yst[j];
+                            c2 Ej1, Dj, Y;
+                            if constexpr (ROLL) {
+                                const float4 x1 = sh_X[(j + 1) * BLOCK + tid];
+                                Ej1 = layer_phase2(kj1, Lj1);
+                                Y = cmul2(c2{make_float2(x1.x, x1.y), make_float2(x1.z, x1.w)}, Ej1);
+                                const c2 rY = cmul2(rj, Y);
+                                const f2 dx = padd(bc(1.f), rY.re), dy = rY.im;
+                                const f2 inv = prcp(pfma(dx, dx, pmul(dy, dy)));
+                                Dj = c2{pmul(dx, inv), pneg(pmul(dy, inv))};
+                            } else {
+                                Ej1 = Est[j + 1];
+                                Dj = Dst[j];
+                                Y = Yst[j];
+                            }
                             Zj = Y;
                             const c2 V = cmulc2(Dj, cmulc2(Dj, Xb));
                             rb = cmulc2(one_minus_sq2(Y), V);
@@ -559,14 +655,8 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                         const c2 gg = cmulc2(Gj, rb);
                         const c2 sr = c2{pmul(bc(Ij.z), rr.re), pneg(pmul(bc(Ij.z), rr.im))};
                         const c2 Hm = c2{pfma(bc(-2.f), gg.re, sr.re), pfma(bc(-2.f), gg.im, sr.im)}; // conj(M) rbar
-                        c2 kkj;
-                        if (top) {
-                            kbar1 = c2{pfma(kj.re, Hm.re, kbar1.re), pfma(kj.re, Hm.im, kbar1.im)};
-                            kkj = c2{pmul(kj.re, kj1.re), pmul(kj.re, kj1.im)};
-                        } else {
-                            kbar1 = cfmac2(kc2(kj), Hm, kbar1);
-                            kkj = cmul2(kc2(kj), kc2(kj1));
-                        }
+                        if (top) kbar1 = c2{pfma(kj.re, Hm.re, kbar1.re), pfma(kj.re, Hm.im, kbar1.im)};
+                        else kbar1 = cfmac2(kc2(kj), Hm, kbar1);
                         acc_fma2(oS + j, rr.re, kkj.re, pneg(rr.im), kkj.im);
                         const c2 Hp = c2{pfma(bc(2.f), gg.re, sr.re), pfma(bc(2.f), gg.im, sr.im)}; // conj(P) rbar
                         if (RES && top) res_k0 = pfma(kj1.re, Hp.re, pmul(kj1.im, Hp.im));
@@ -587,14 +677,26 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                                             const int slot = eq_cnt + __popc(em & ((1u << lane) - 1u));
                                             if constexpr (RES)
                                                 sh_eq[warp][EQF - 1][slot] = make_float2(half(k0h, h) * half(wres, h), 0.f);
-                                            sh_eq[warp][0][slot] = make_float2(half(kjm1.re, h), half(kjm1.im, h));
-                                            sh_eq[warp][1][slot] = make_float2(half(kj.re, h), half(kj.im, h));
-                                            sh_eq[warp][2][slot] = make_float2(half(kj1.re, h), half(kj1.im, h));
-                                            sh_eq[warp][3][slot] = make_float2(half(Zj.re, h), half(Zj.im, h));
-                                            sh_eq[warp][4][slot] = make_float2(half(Xb_up.re, h), half(Xb_up.im, h));
+                                            if constexpr (ROLL) {
+                                                sh_eq[warp][0][slot] = make_float2(half(k0h, h), half(k0l, h));
+                                                sh_eq[warp][1][slot] = make_float2(half(Zj.re, h), half(Zj.im, h));
+                                                sh_eq[warp][2][slot] = make_float2(half(Xb_up.re, h), half(Xb_up.im, h));
+                                            } else {
+                                                sh_eq[warp][0][slot] = make_float2(half(kjm1.re, h), half(kjm1.im, h));
+                                                sh_eq[warp][1][slot] = make_float2(half(kj.re, h), half(kj.im, h));
+                                                sh_eq[warp][2][slot] = make_float2(half(kj1.re, h), half(kj1.im, h));
+                                                sh_eq[warp][3][slot] = make_float2(half(Zj.re, h), half(Zj.im, h));
+                                                sh_eq[warp][4][slot] = make_float2(half(Xb_up.re, h), half(Xb_up.im, h));
+                                            }
                                             sh_eqj[warp][slot] = j;
                                         }
                                         eq_cnt += __popc(em);
+                                        if constexpr (ROLL) {
+                                            if (eq_cnt >= 32) {
+                                                __syncwarp();
+                                                eq_drain(32);
+                                            }
+                                        }
                                     }
                                 }
                             }
@@ -602,8 +704,8 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                             f2 inv = prcp(pmax(m2, bc(1e-30f)));
                             if constexpr (decltype(EDG)::value) inv = psel(edge, bc(0.f), inv);
                             const f2 ur = pmul(kq.re, inv), ui = pneg(pmul(kq.im, inv));
-                            accr[oUr + j - 1] = padd(accr[oUr + j - 1], ur);
-                            accr[oUi + j - 1] = padd(accr[oUi + j - 1], ui);
+                            acc_add(oUr + j - 1, ur);
+                            acc_add(oUi + j - 1, ui);
                             if constexpr (RES) res_sum = padd(res_sum, ur);
                         }
                         Xb_up = Xb_in;
@@ -615,15 +717,22 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                             const f2 m2 = pfma(kj.re, kj.re, pmul(kj.im, kj.im));
                             const f2 inv = prcp(pmax(m2, bc(1e-30f)));
                             const f2 ur = pmul(kk.re, inv), ui = pneg(pmul(kk.im, inv));
-                            accr[oUr + j] = padd(accr[oUr + j], ur);
-                            accr[oUi + j] = padd(accr[oUi + j], ui);
+                            acc_add(oUr + j, ur);
+                            acc_add(oUi + j, ui);
                             if constexpr (RES) res_sum = padd(res_sum, ur);
                         }
                     };
                     auto sweep = [&](auto EDG) __attribute__((always_inline)) {
+                        if constexpr (ROLL) {
+                            if (n >= 1) adj_step(0, Pos<kYes>{}, Pos<kNo>{}, EDG);
+#pragma unroll kPairDeepUnroll
+                            for (int j = 1; j <= n - 1; ++j) adj_step(j, Pos<kNo>{}, Pos<kNo>{}, EDG);
+                            adj_step(n, Pos<kRt>{}, Pos<kYes>{}, EDG);
+                        } else {
 #pragma unroll
-                        for (int j = 0; j <= NM; ++j)
-                            if (j <= n) adj_step(j, EDG);
+                            for (int j = 0; j <= NM; ++j)
+                                if (j <= n) adj_step(j, Pos<kRt>{}, Pos<kRt>{}, EDG);
+                        }
                         if constexpr (decltype(EDG)::value) {
                             while (eq_cnt >= 32) {
                                 __syncwarp();
@@ -652,8 +761,8 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
             // ---- CTA reduction of the item's partial sums into sh_raw ----
             __syncthreads();
             for (int i = tid; i < s_cnt; i += BLOCK) consume(i);
-            static_assert(NACC <= 32, "register partials exceed one reduction batch");
-            if constexpr (GRAD) {
+            static_assert(ROLL || NACC <= 32, "register partials exceed one reduction batch");
+            if constexpr (GRAD && !ROLL) {
 #pragma unroll
                 for (int t = 0; t < NACC; ++t) {
                     float v = accr[t].x + accr[t].y;
@@ -676,7 +785,31 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                     }
                 }
                 __syncthreads();
-            } // GRAD
+            } // GRAD && !ROLL
+            if constexpr (ROLL) { // shared-memory partials, 32 raw sums at a time
+                const int nraw = 4 * n + 3;
+                for (int base = 0; base < nraw; base += 32) {
+                    const int cnt = min(32, nraw - base);
+                    for (int c = 0; c < cnt; ++c) {
+                        const int i = base + c;
+                        const int idx = i < n ? i
+                                        : i < 2 * n + 1 ? NM + (i - n)
+                                        : i < 3 * n + 2 ? 2 * NM + 1 + (i - 2 * n - 1)
+                                                        : 3 * NM + 2 + (i - 3 * n - 2);
+                        float v = sh_acc[idx * BLOCK + tid];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+                        if (lane == 0) sh_red[warp][c] = (double)v;
+                    }
+                    __syncthreads();
+                    if (tid < cnt) {
+                        double sum = 0.0;
+                        for (int w = 0; w < WARPS; ++w) sum += sh_red[w][tid];
+                        sh_raw[base + tid] = sum;
+                    }
+                    __syncthreads();
+                }
+            }
             {   // loglik (float pair), d/dscale, d/dbkg, d/d ln(dQ scale)
                 float h = ll_hi, l = ll_lo, a1 = gsc_acc, a2 = gbk_acc, a3 = gres_acc.x + gres_acc.y;
 #pragma unroll
@@ -749,16 +882,36 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
 }
 
 template <int MODE, int NMAX, int KC>
+cudaError_t pair_smem_attr()
+{
+    // the default cap on dynamic shared memory is 48 KB less the static use
+    constexpr size_t dyn = PairTraits<MODE, NMAX>::DYN;
+    if (dyn > 0)
+        return cudaFuncSetAttribute(nr_pair_kernel<MODE, NMAX, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)dyn);
+    return cudaSuccess;
+}
+
+template <int MODE, int NMAX, int KC>
 cudaError_t pair_launch_k(int grid, const KernelArgs &a, const QuadConst &qc, cudaStream_t st)
 {
-    nr_pair_kernel<MODE, NMAX, KC><<<grid, kPairBlock, 0, st>>>(a, qc);
+    static bool attr_done = false; // per process: the attribute belongs to the function
+    if (!attr_done) {
+        const cudaError_t e = pair_smem_attr<MODE, NMAX, KC>();
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    nr_pair_kernel<MODE, NMAX, KC><<<grid, kPairBlock, PairTraits<MODE, NMAX>::DYN, st>>>(a, qc);
     return cudaGetLastError();
 }
 
 template <int MODE, int NMAX, int KC>
 cudaError_t pair_occupancy_k(int *blocks)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, nr_pair_kernel<MODE, NMAX, KC>, kPairBlock, 0);
+    const cudaError_t e = pair_smem_attr<MODE, NMAX, KC>();
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, nr_pair_kernel<MODE, NMAX, KC>, kPairBlock,
+                                                         PairTraits<MODE, NMAX>::DYN);
 }
 
 // the 1-layer kernels are also compiled for the workloads' quadrature
@@ -785,9 +938,15 @@ cudaError_t pair_occupancy_one(int K, int *blocks)
 
 } // namespace
 
+// gradient buckets of the paired kernels
+#define NR_PAIR_GRAD_BUCKETS(X) X(1) X(2) X(4) X(8) X(12) X(16) X(20)
+
 bool pair_eligible(int mode, int nmax, int K)
 {
-    return NR_PAIR && K >= 3 && (is_grad_mode(mode) ? (nmax == 1 || nmax == 2) : nmax == 1);
+    if (!NR_PAIR || K < 3) return false;
+    if (!is_grad_mode(mode)) return nmax == 1;
+    if (nmax <= 2) return nmax >= 1;
+    return NR_PAIR_DEEP_FROM > 0 && nmax >= NR_PAIR_DEEP_FROM && nmax <= 20;
 }
 
 int pair_block_threads() { return kPairBlock; }
@@ -796,18 +955,32 @@ cudaError_t pair_occupancy(int mode, int nmax, int K, int *blocks)
 {
     if (mode == kModel) return pair_occupancy_one<kModel, 1>(K, blocks);
     if (mode == kLoglik) return pair_occupancy_one<kLoglik, 1>(K, blocks);
-    if (mode == kGradRes) return nmax == 1 ? pair_occupancy_one<kGradRes, 1>(K, blocks)
-                                           : pair_occupancy_one<kGradRes, 2>(K, blocks);
-    return nmax == 1 ? pair_occupancy_one<kGrad, 1>(K, blocks) : pair_occupancy_one<kGrad, 2>(K, blocks);
+    if (mode == kGradRes) {
+#define X(B) if (nmax == B) return pair_occupancy_one<kGradRes, B>(K, blocks);
+        NR_PAIR_GRAD_BUCKETS(X)
+#undef X
+    } else {
+#define X(B) if (nmax == B) return pair_occupancy_one<kGrad, B>(K, blocks);
+        NR_PAIR_GRAD_BUCKETS(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_pair(int mode, int nmax, int grid, const KernelArgs &a, const QuadConst &qc, cudaStream_t st)
 {
     if (mode == kModel) return pair_launch_one<kModel, 1>(grid, a, qc, st);
     if (mode == kLoglik) return pair_launch_one<kLoglik, 1>(grid, a, qc, st);
-    if (mode == kGradRes) return nmax == 1 ? pair_launch_one<kGradRes, 1>(grid, a, qc, st)
-                                           : pair_launch_one<kGradRes, 2>(grid, a, qc, st);
-    return nmax == 1 ? pair_launch_one<kGrad, 1>(grid, a, qc, st) : pair_launch_one<kGrad, 2>(grid, a, qc, st);
+    if (mode == kGradRes) {
+#define X(B) if (nmax == B) return pair_launch_one<kGradRes, B>(grid, a, qc, st);
+        NR_PAIR_GRAD_BUCKETS(X)
+#undef X
+    } else {
+#define X(B) if (nmax == B) return pair_launch_one<kGrad, B>(grid, a, qc, st);
+        NR_PAIR_GRAD_BUCKETS(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
 }
 
 } // namespace nrimpl
