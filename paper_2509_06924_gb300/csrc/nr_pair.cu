@@ -47,7 +47,7 @@
 // CTAs per SM asked of the rolled (>= 3 layer) gradient kernels; their
 // shared-memory partials and X_j usually set the occupancy first
 #ifndef NR_PAIR_MINB_DEEP
-#define NR_PAIR_MINB_DEEP 3
+#define NR_PAIR_MINB_DEEP 4
 #endif
 // gradient buckets [NR_PAIR_DEEP_FROM, 20] run the rolled paired kernel
 // (NR_PAIR_DEEP_FROM 0: none); deeper buckets keep the one-evaluation kernel,
@@ -55,7 +55,12 @@
 #ifndef NR_PAIR_DEEP_FROM
 #define NR_PAIR_DEEP_FROM 4
 #endif
-// CTAs per SM of the 1-layer forward (model / loglik) kernels
+// 1: the runtime-n forward bucket (model / loglik of stacks with n != 1)
+// runs the paired kernel too
+#ifndef NR_PAIR_FWD_ANY
+#define NR_PAIR_FWD_ANY 1
+#endif
+// CTAs per SM of the forward (model / loglik) kernels
 #ifndef NR_PAIR_MINB_FWD
 #define NR_PAIR_MINB_FWD 8
 #endif
@@ -247,6 +252,9 @@ template <int MODE, int NMAX>
 struct PairTraits {
     static constexpr bool GRAD = MODE == kGrad || MODE == kGradRes;
     static constexpr bool ROLL = GRAD && NMAX > 2;
+    // rolled forward sweep: the rolled gradient kernels and the runtime-n
+    // forward kernel (NMAX = 0, any layer count)
+    static constexpr bool RFWD = ROLL || NMAX == 0;
     static constexpr int NACC = 4 * NMAX + 3;
     static constexpr int MINB = !GRAD ? NR_PAIR_MINB_FWD : NMAX == 1 ? NR_PAIR_MINB1
                                 : NMAX == 2 ? NR_PAIR_MINB2 : NR_PAIR_MINB_DEEP;
@@ -262,9 +270,9 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
     constexpr bool GRAD = PT::GRAD;
     constexpr bool ROLL = PT::ROLL;
     constexpr bool LIK = MODE != kModel;
-    static_assert(GRAD ? (NMAX >= 1 && NMAX <= NR_MAX_LAYERS) : NMAX == 1,
-                  "paired kernel: gradients of any bucket, 1-layer forward");
-    constexpr int NM = NMAX;
+    static_assert(GRAD ? (NMAX >= 1 && NMAX <= NR_MAX_LAYERS) : (NMAX == 1 || NMAX == 0),
+                  "paired kernel: gradient buckets, 1-layer and runtime-n forward");
+    constexpr int NM = NMAX > 0 ? NMAX : NR_MAX_LAYERS; // shared-memory capacity in layers
     constexpr int BLOCK = kPairBlock;
     constexpr int WARPS = BLOCK / 32;
     constexpr bool RES = MODE == kGradRes;
@@ -536,7 +544,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                 Xbelow = Xj;
                 kbelow = kj;
             };
-            if constexpr (ROLL) {
+            if constexpr (PT::RFWD) {
                 fwd_step(n, Pos<kRt>{}, Pos<kYes>{});
 #pragma unroll kPairDeepUnroll
                 for (int j = n - 1; j >= 1; --j) fwd_step(j, Pos<kNo>{}, Pos<kNo>{});
@@ -944,7 +952,7 @@ cudaError_t pair_occupancy_one(int K, int *blocks)
 bool pair_eligible(int mode, int nmax, int K)
 {
     if (!NR_PAIR || K < 3) return false;
-    if (!is_grad_mode(mode)) return nmax == 1;
+    if (!is_grad_mode(mode)) return nmax == 1 || (NR_PAIR_FWD_ANY && nmax == 0);
     if (nmax <= 2) return nmax >= 1;
     return NR_PAIR_DEEP_FROM > 0 && nmax >= NR_PAIR_DEEP_FROM && nmax <= 20;
 }
@@ -953,8 +961,10 @@ int pair_block_threads() { return kPairBlock; }
 
 cudaError_t pair_occupancy(int mode, int nmax, int K, int *blocks)
 {
-    if (mode == kModel) return pair_occupancy_one<kModel, 1>(K, blocks);
-    if (mode == kLoglik) return pair_occupancy_one<kLoglik, 1>(K, blocks);
+    if (mode == kModel) return nmax == 1 ? pair_occupancy_one<kModel, 1>(K, blocks)
+                                         : pair_occupancy_one<kModel, 0>(K, blocks);
+    if (mode == kLoglik) return nmax == 1 ? pair_occupancy_one<kLoglik, 1>(K, blocks)
+                                          : pair_occupancy_one<kLoglik, 0>(K, blocks);
     if (mode == kGradRes) {
 #define X(B) if (nmax == B) return pair_occupancy_one<kGradRes, B>(K, blocks);
         NR_PAIR_GRAD_BUCKETS(X)
@@ -969,8 +979,10 @@ cudaError_t pair_occupancy(int mode, int nmax, int K, int *blocks)
 
 cudaError_t launch_pair(int mode, int nmax, int grid, const KernelArgs &a, const QuadConst &qc, cudaStream_t st)
 {
-    if (mode == kModel) return pair_launch_one<kModel, 1>(grid, a, qc, st);
-    if (mode == kLoglik) return pair_launch_one<kLoglik, 1>(grid, a, qc, st);
+    if (mode == kModel) return nmax == 1 ? pair_launch_one<kModel, 1>(grid, a, qc, st)
+                                         : pair_launch_one<kModel, 0>(grid, a, qc, st);
+    if (mode == kLoglik) return nmax == 1 ? pair_launch_one<kLoglik, 1>(grid, a, qc, st)
+                                          : pair_launch_one<kLoglik, 0>(grid, a, qc, st);
     if (mode == kGradRes) {
 #define X(B) if (nmax == B) return pair_launch_one<kGradRes, B>(grid, a, qc, st);
         NR_PAIR_GRAD_BUCKETS(X)
