@@ -225,8 +225,23 @@ def cpu_baseline(wl, target_s: float = 10.0) -> dict:
     oracle.batch("grad", sub.n_layers, sub.params, sub.dataset, sub.q_off, sub.q, sub.dq, sub.r_obs, sub.r_err,
                  sub.n_quad)
     dt = time.perf_counter() - t0
-    return {"value": sub.evals / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {count} of {wl.n_stacks} stacks ({sub.evals} evals, {dt:.1f} s, fwd + dual-number grad)"}
+    out = {"value": sub.evals / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"first {count} of {wl.n_stacks} stacks ({sub.evals} evals, {dt:.1f} s, fwd + dual-number grad)"}
+    # the same oracle on one core, on a ~2 s sample
+    one = wl.subset(np.arange(1))
+    t0 = time.perf_counter()
+    oracle.batch("grad", one.n_layers, one.params, one.dataset, one.q_off, one.q, one.dq, one.r_obs, one.r_err,
+                 one.n_quad, n_threads=1)
+    dt1 = time.perf_counter() - t0
+    c1 = int(min(wl.n_stacks, max(1, 2.0 / max(dt1, 1e-6))))
+    sub1 = wl.subset(np.arange(c1))
+    t0 = time.perf_counter()
+    oracle.batch("grad", sub1.n_layers, sub1.params, sub1.dataset, sub1.q_off, sub1.q, sub1.dq, sub1.r_obs,
+                 sub1.r_err, sub1.n_quad, n_threads=1)
+    dt1 = time.perf_counter() - t0
+    out["value_1core"] = sub1.evals / dt1
+    out["sample_1core"] = f"first {c1} stacks ({sub1.evals} evals, {dt1:.1f} s, one thread)"
+    return out
 
 
 def run_reference(args):
