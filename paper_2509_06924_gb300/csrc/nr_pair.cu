@@ -1,6 +1,6 @@
-// nr_pair.cu -- the kernels of the 1- and 2-layer gradient buckets and of
-// the 1-layer forward bucket (model, log-likelihood) with two evaluations
-// per thread in paired FP32 arithmetic (sm_100-family add/mul/fma.rn.f32x2).
+// nr_pair.cu -- the kernels of the gradient buckets up to 20 layers and of
+// both forward buckets (model, log-likelihood) with two evaluations per
+// thread in paired FP32 arithmetic (sm_100-family add/mul/fma.rn.f32x2).
 //
 // The mixed-precision gradient evaluation is bound by instruction issue, not
 // by the FP32 pipes: about 60 % of the issued instructions are FP32 adds,
@@ -19,11 +19,12 @@
 // The forward modes run the same code up to the smearing sum (model: write
 // scale S + bkg; log-likelihood: the residual terms) and no adjoint.
 // Everything else follows the one-evaluation-per-thread kernel (nr_mixed.cu)
-// step for step, with the same double-float guards, the same stored
-// intermediates (1-2 layers keep all of them in registers) and the same
-// interior critical-edge treatment: evaluations whose k_j falls in the edge
-// band are queued per warp and drained by the scalar edge adjoint, one entry
-// per lane.  A thread carries two adjacent evaluation slots of its tile.
+// step for step, with the same double-float guards, the same split between
+// stored intermediates (1-2 layers keep all of them in registers) and
+// rolled sweeps that recompute them (deeper stacks), and the same interior
+// critical-edge treatment: evaluations whose k_j falls in the edge band are
+// queued per warp and drained by the scalar edge adjoint, one entry per
+// lane.  A thread carries two adjacent evaluation slots of its tile.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -44,14 +45,15 @@
 #ifndef NR_PAIR_MINB2
 #define NR_PAIR_MINB2 3
 #endif
-// CTAs per SM asked of the rolled (>= 3 layer) gradient kernels; their
+// CTAs per SM asked of the rolled (4-20 layer bucket) gradient kernels; their
 // shared-memory partials and X_j usually set the occupancy first
 #ifndef NR_PAIR_MINB_DEEP
 #define NR_PAIR_MINB_DEEP 4
 #endif
 // gradient buckets [NR_PAIR_DEEP_FROM, 20] run the rolled paired kernel
-// (NR_PAIR_DEEP_FROM 0: none); deeper buckets keep the one-evaluation kernel,
-// whose shared-memory state per evaluation is half as large
+// (NR_PAIR_DEEP_FROM 0: none).  The 32- and 64-layer buckets keep the
+// one-evaluation kernel: two evaluations' X_j and partials per thread would
+// leave room for one 128-thread CTA per SM at 32 layers, and none at 64.
 #ifndef NR_PAIR_DEEP_FROM
 #define NR_PAIR_DEEP_FROM 4
 #endif
@@ -64,7 +66,7 @@
 #ifndef NR_PAIR_MINB_FWD
 #define NR_PAIR_MINB_FWD 8
 #endif
-// 0: the 1- and 2-layer gradient buckets keep the one-evaluation kernel
+// 0: every bucket keeps the one-evaluation kernel
 #ifndef NR_PAIR
 #define NR_PAIR 1
 #endif
@@ -244,7 +246,8 @@ __device__ __forceinline__ c2 mobius2(c2 r, c2 Y, c2 &D)
 
 // ---------------------------------------------------------------- traits --
 // STORE (1-2 layer gradients): unrolled sweeps, every forward intermediate
-// and the partial gradients in registers.  ROLL (3-64 layers): rolled sweeps
+// and the partial gradients in registers.  ROLL (the 4-20 layer buckets,
+// i.e. 3-20 layers): rolled sweeps
 // peeled at the first and last steps; X_j (both halves) and the partial
 // gradients (both halves summed, one float per thread) in shared memory;
 // k, r and E recomputed in the adjoint; edge entries keep the node k_0.
