@@ -161,10 +161,14 @@ KERNEL_SOURCES = ("nr_device.cuh", "nr_mixed.cu", "nr_pair.cu")
 
 def kernel_source_hash() -> str:
     """Hash of the gradient kernels' sources (shared header, one- and
-    two-evaluations-per-thread kernels), in that order."""
+    two-evaluations-per-thread kernels, in that order) with // comments and
+    whitespace removed, so that an edit of the comments alone does not mark
+    a capture of the same code as stale."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2509_06924_gb300", "csrc", f), "rb").read())
+        text = open(os.path.join(ROOT, "paper_2509_06924_gb300", "csrc", f), encoding="utf-8").read()
+        code = "".join("".join(line.split("//", 1)[0].split()) for line in text.splitlines())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 
