@@ -179,8 +179,9 @@ def profile_record(workload: str) -> dict:
     rec = {}
     try:
         for line in open(path):
-            if ":" in line and not line.startswith(" "):
-                k, v = line.split(":", 1)
+            # "key: value" (keys may hold a colon themselves, as in sha256[:16])
+            if ": " in line and not line.startswith(" "):
+                k, v = line.split(": ", 1)
                 rec[k.strip()] = v.strip()
     except OSError:
         return {}

@@ -148,3 +148,39 @@ def test_flop_table_is_monotone_and_positive():
     # the 1-layer count, term by term: forward 166, seed 11, adjoint 156
     assert abs(bench.flops_per_eval(1, 21) - (166 + 11 + 156 + 15 / 21)) < 1e-9
     assert abs(bench.peak_fp32_tflops() - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+
+
+def test_profile_record_reads_the_summary_format(tmp_path, monkeypatch):
+    """The bench takes traffic and FP32 counts from a committed ncu summary
+    only while its kernel-source hash matches; keys may contain a colon."""
+    import bench
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "nr_mixed_grad_w.txt").write_text(
+        "kernel: k<2, 1, 21>(A, B)\nkernel source sha256[:16]: abc\ndram bytes per full launch: 123\n"
+        "fp32 lane ops per eval: 4.5\n\ncommand: ncu --a b: c\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc")
+    rec = bench.profile_record("w")
+    assert rec["dram bytes per full launch"] == "123" and rec["fp32 lane ops per eval"] == "4.5"
+    assert rec["command"] == "ncu --a b: c"
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "other")
+    assert bench.profile_record("w") == {}
+
+
+def test_kernel_source_hash_ignores_comments_only(tmp_path, monkeypatch):
+    import shutil
+
+    import bench
+    src = os.path.join(ROOT, "paper_2509_06924_gb300", "csrc")
+    dst = tmp_path / "paper_2509_06924_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(src, f), dst / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_source_hash()
+    p = dst / bench.KERNEL_SOURCES[-1]
+    text = p.read_text()
+    p.write_text("// a comment\n" + text.replace("\n", "  // trailing\n", 3))
+    assert bench.kernel_source_hash() == h0
+    p.write_text(text + "\nstatic int extra_symbol;\n")
+    assert bench.kernel_source_hash() != h0
