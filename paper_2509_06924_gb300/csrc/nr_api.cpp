@@ -161,7 +161,6 @@ struct Plan {
     int32_t S = 0, D = 0, K = 0;
     std::vector<int32_t> n_layers, dataset;
     std::vector<int64_t> q_off;
-    uint64_t hash = 0;
     // derived
     int64_t total_params = 0, total_out = 0, total_q = 0, evals = 0;
     WorkList fwd, grad;
@@ -173,15 +172,7 @@ struct Plan {
     uint64_t last_use = 0;
 };
 
-uint64_t fnv(uint64_t h, const void *data, size_t n)
-{
-    const unsigned char *p = static_cast<const unsigned char *>(data);
-    for (size_t i = 0; i < n; ++i) {
-        h ^= p[i];
-        h *= 1099511628211ull;
-    }
-    return h;
-}
+
 
 } // namespace
 
@@ -240,20 +231,6 @@ nr_status validate(const nr_batch *b)
             return fail(NR_EINVAL, "stack %d: dataset %d outside [0, %d)", s, b->dataset[s], b->n_datasets);
     }
     return NR_OK;
-}
-
-uint64_t batch_hash(const nr_batch *b, int K)
-{
-    uint64_t h = 1469598103934665603ull;
-    h = fnv(h, &b->n_stacks, sizeof b->n_stacks);
-    h = fnv(h, &b->n_datasets, sizeof b->n_datasets);
-    h = fnv(h, &K, sizeof K);
-    if (b->n_stacks > 0) {
-        h = fnv(h, b->n_layers, sizeof(int32_t) * b->n_stacks);
-        h = fnv(h, b->dataset, sizeof(int32_t) * b->n_stacks);
-        h = fnv(h, b->q_off, sizeof(int64_t) * (b->n_datasets + 1));
-    }
-    return h;
 }
 
 bool same_meta(const Plan &p, const nr_batch *b, int K)
@@ -423,10 +400,15 @@ nr_status build_fp64(nr_ctx *ctx, Plan &pl)
 nr_status get_plan(nr_ctx *ctx, const nr_batch *b, int mode, Plan **out)
 {
     const int K = ctx->qc.K;
-    const uint64_t h = batch_hash(b, K);
+    // At most 8 cached plans, the most recently used first: the sizes and then
+    // a memcmp of the host metadata decide (a mismatch usually ends early).
+    // A per-call hash of the metadata cost more on the host than this scan.
     Plan *pl = nullptr;
     for (auto &p : ctx->plans)
-        if (p->hash == h && same_meta(*p, b, K)) { pl = p.get(); break; }
+        if (p->last_use == ctx->clock && same_meta(*p, b, K)) { pl = p.get(); break; }
+    if (!pl)
+        for (auto &p : ctx->plans)
+            if (same_meta(*p, b, K)) { pl = p.get(); break; }
     if (!pl) {
         nr_status st = validate(b);
         if (st != NR_OK) return st;
@@ -440,7 +422,6 @@ nr_status get_plan(nr_ctx *ctx, const nr_batch *b, int mode, Plan **out)
         np->S = b->n_stacks;
         np->D = b->n_datasets;
         np->K = K;
-        np->hash = h;
         if (np->S > 0) {
             np->n_layers.assign(b->n_layers, b->n_layers + np->S);
             np->dataset.assign(b->dataset, b->dataset + np->S);
