@@ -260,8 +260,10 @@ def test_paired_gradient_kernel_orders_and_buckets(K):
     wl = custom_workload(stacks, datasets, K=K)
     ref_ll, ref_g, ref_r = oracle.batch("grad_res", wl.n_layers, wl.params, wl.dataset, wl.q_off, wl.q, wl.dq,
                                         wl.r_obs, wl.r_err, K)
-    ref = {"ll": ref_ll, "g": ref_g}
-    assert_parity(wl, run_gpu(wl, modes=("grad",)), ref)
+    ref = {"ll": ref_ll, "g": ref_g, "m": run_oracle(wl, modes=("model",))["m"]}
+    # model and log-likelihood run the paired forward kernels (the 1-layer
+    # bucket and the runtime-n bucket with n = 0 and 2)
+    assert_parity(wl, run_gpu(wl), ref)
     # several items per stack and a tile shorter than the widest, with the
     # resolution derivative through the same kernel
     ctx = nr.Context(n_quad=K, chunk_q=9, tile_q=5)
