@@ -207,9 +207,18 @@ def fp64_fd_baseline(wl, stacks: int = 1024) -> dict:
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
+    # the plain FP64 forward alone (model, smearing and log-likelihood)
+    ctx.loglik(b)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        ctx.loglik(b)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1) / reps
     ctx.close()
     return {"value": sub.evals / (ms * 1e-3), "unit": UNIT, "sample": f"first {sub.n_stacks} stacks",
-            "ms_per_call": ms}
+            "ms_per_call": ms, "forward_value": sub.evals / (ms_fwd * 1e-3), "forward_ms_per_call": ms_fwd}
 
 
 def cpu_baseline(wl, target_s: float = 10.0) -> dict:
