@@ -242,6 +242,13 @@ bool same_meta(const Plan &p, const nr_batch *b, int K)
            std::memcmp(p.q_off.data(), b->q_off, sizeof(int64_t) * (p.D + 1)) == 0;
 }
 
+// Work items per resident CTA below which stacks are cut into Q-range
+// chunks (the persistent queue's tail is then at most 1 / kMinWaves of a launch)
+#ifndef NR_MIN_WAVES
+#define NR_MIN_WAVES 4
+#endif
+constexpr int64_t kMinWaves = NR_MIN_WAVES;
+
 int tile_for(const nr_ctx *ctx, int mode, int nmax)
 {
     int tq = mixed_tile_q(mode, nmax, ctx->qc.K);
@@ -298,8 +305,8 @@ nr_status build_worklist(nr_ctx *ctx, Plan &pl, int mode, WorkList &wl)
         int64_t chunk = max_len;
         if (ctx->opt.chunk_q > 0) {
             chunk = ctx->opt.chunk_q;
-        } else if (nst < 4 * resident && max_len > 0) {
-            const int64_t want = (4 * resident + nst - 1) / nst; // pieces per stack
+        } else if (nst < kMinWaves * resident && max_len > 0) {
+            const int64_t want = (kMinWaves * resident + nst - 1) / nst; // pieces per stack
             chunk = std::max<int64_t>((max_len + want - 1) / want, g.tile_q);
             chunk = (chunk + g.tile_q - 1) / g.tile_q * g.tile_q;
         }
