@@ -128,8 +128,11 @@ void nr_destroy(nr_ctx *ctx);
 const char *nr_last_error(void);
 
 /* Validate the batch metadata, build its work list on the device and, when
- * the context was created with autotune = 1, time candidate launch shapes
- * on the batch's own data.  Optional: the compute calls plan on first use.
+ * the context was created with autotune = 1 (NR_MIXED, device-memory
+ * batches), time candidate launch shapes on the batch's own data: per
+ * register bucket the two-evaluations-per-thread and the one-evaluation
+ * kernel at the widest tile and at half of it; the fastest is kept for the
+ * plan.  Optional: the compute calls plan on first use (without tuning).
  * Must precede CUDA-graph capture of a compute call, which then allocates
  * nothing and copies no metadata.  Errors: NR_EINVAL, NR_ENOMEM, NR_ECUDA. */
 nr_status nr_plan(nr_ctx *ctx, const nr_batch *batch);

@@ -146,6 +146,7 @@ struct Group {
     int item_count = 0;
     int grid = 0;
     int tile_q = 0;
+    bool pair = true; // the paired kernel where it applies (the autotuner may clear it)
 };
 
 // Work list of one mode family (forward = model/loglik, or gradient).
@@ -154,6 +155,7 @@ struct WorkList {
     DevBuf d_stacks, d_items, d_partials, d_done, d_ticket;
     int64_t partial_doubles = 0;
     int chunk_q = 0;
+    bool tuned = false; // launch shapes chosen by timing (nr_plan, autotune = 1)
 };
 
 struct Plan {
@@ -496,9 +498,97 @@ nr_status launch_device(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, floa
         a.n_items = G.item_count;
         a.tile_q = G.tile_q;
         a.ticket = wl.d_ticket.as<int32_t>() + 2 * g;
-        cudaError_t e = launch_mixed(mode, G.nmax, G.grid, a, ctx->qc, st);
+        cudaError_t e = launch_mixed(mode, G.nmax, G.grid, a, ctx->qc, st, G.pair);
         if (e != cudaSuccess) return fail(NR_ECUDA, "mixed launch (bucket %d): %s", G.nmax, cudaGetErrorString(e));
     }
+    return NR_OK;
+}
+
+// Autotuning (nr_plan on a context created with autotune = 1, device-memory
+// batches, NR_MIXED): for every register bucket of a work list, time the
+// candidate launch shapes on the batch's own data and keep the fastest.  The
+// candidates are the paired and the one-evaluation kernel (where both apply)
+// at the widest tile and at half of it, each at the grid its occupancy
+// allows.  The work items (chunking) stay as planned.  Outputs go to scratch
+// buffers; the device status word sees the timing launches like any call.
+nr_status autotune_worklist(nr_ctx *ctx, Plan &pl, const nr_batch *b, bool grad)
+{
+    WorkList &wl = grad ? pl.grad : pl.fwd;
+    if (pl.S == 0 || wl.groups.empty() || wl.tuned) return NR_OK;
+    const bool lik = b->r_obs && b->r_err;
+    const int mode = grad ? kGrad : (lik ? kLoglik : kModel);
+    if (mode != kModel && !lik) return NR_OK;
+    const int K = ctx->qc.K;
+    DevBuf out, ll, gr;
+    if (mode == kModel) NR_CUDA(out.ensure(sizeof(float) * std::max<int64_t>(pl.total_out, 1)));
+    else NR_CUDA(ll.ensure(sizeof(double) * pl.S));
+    if (grad) NR_CUDA(gr.ensure(sizeof(double) * std::max<int64_t>(pl.total_params, 1)));
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    NR_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    KernelArgs a{};
+    a.params = b->params;
+    a.q = b->q;
+    a.dq = b->dq;
+    a.r_obs = b->r_obs;
+    a.r_err = b->r_err;
+    a.r_out = out.as<float>();
+    a.ll_out = ll.as<double>();
+    a.grad_out = gr.as<double>();
+    a.status = ctx->d_status;
+    a.stacks = wl.d_stacks.as<StackInfo>();
+    a.partials = wl.d_partials.as<double>();
+    a.stack_done = wl.d_done.as<int32_t>();
+    constexpr int kReps = 3;
+    for (size_t g = 0; g < wl.groups.size() && ce == cudaSuccess; ++g) {
+        Group &G = wl.groups[g];
+        a.items = wl.d_items.as<WorkItem>() + G.item_begin;
+        a.n_items = G.item_count;
+        a.ticket = wl.d_ticket.as<int32_t>() + 2 * g;
+        float best_ms = 0.f;
+        Group best = G;
+        for (int pv = 1; pv >= 0 && ce == cudaSuccess; --pv) {
+            if (pv == 1 && !pair_eligible(mode, G.nmax, K)) continue;
+            int occ = 1;
+            ce = mixed_occupancy(mode, G.nmax, K, &occ, pv == 1);
+            if (ce != cudaSuccess) break;
+            int grid = (int)std::min<int64_t>(G.item_count, (int64_t)ctx->sms * std::max(occ, 1));
+            if (ctx->opt.grid_ctas > 0) grid = std::min(G.item_count, ctx->opt.grid_ctas);
+            grid = std::max(grid, 1);
+            int tmax = mixed_tile_q(mode, G.nmax, K, pv == 1);
+            if (ctx->opt.tile_q > 0) tmax = std::min(tmax, ctx->opt.tile_q);
+            tmax = std::max(tmax, 1);
+            for (int tq : {tmax, tmax / 2}) {
+                if (tq < 1) continue;
+                a.tile_q = tq;
+                ce = launch_mixed(mode, G.nmax, grid, a, ctx->qc, st, pv == 1); // warm-up
+                if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
+                for (int r = 0; r < kReps && ce == cudaSuccess; ++r)
+                    ce = launch_mixed(mode, G.nmax, grid, a, ctx->qc, st, pv == 1);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                if (ce != cudaSuccess) break;
+                if (best_ms == 0.f || ms < best_ms) {
+                    best_ms = ms;
+                    best.pair = pv == 1;
+                    best.tile_q = tq;
+                    best.grid = grid;
+                }
+            }
+        }
+        if (ce == cudaSuccess) G = best;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    const cudaError_t se = cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (ce == cudaSuccess) ce = se;
+    if (ce != cudaSuccess) return fail(NR_ECUDA, "autotune: %s", cudaGetErrorString(ce));
+    wl.tuned = true;
     return NR_OK;
 }
 
@@ -630,6 +720,10 @@ nr_status nr_plan(nr_ctx *ctx, const nr_batch *batch)
     Plan *pl = nullptr;
     nr_status st = get_plan(ctx, batch, kModel, &pl);
     if (st == NR_OK) st = get_plan(ctx, batch, kGrad, &pl);
+    if (st == NR_OK && ctx->opt.autotune && ctx->opt.precision == NR_MIXED && batch->memory == NR_MEM_DEVICE) {
+        st = autotune_worklist(ctx, *pl, batch, false);
+        if (st == NR_OK) st = autotune_worklist(ctx, *pl, batch, true);
+    }
     return st;
 }
 

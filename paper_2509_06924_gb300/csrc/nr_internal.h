@@ -79,13 +79,15 @@ struct KernelArgs {
 // Mixed-precision kernels.  `nmax` is the register-array capacity bucket of
 // the launch (every stack of the launch has n <= nmax; nmax = 1 means exactly
 // one layer); 0 selects the runtime-n forward kernel (model / loglik modes).
+// allow_pair = false keeps the one-evaluation kernel where the paired kernel
+// (nr_pair.cu) would otherwise run (the autotuner times both).
 int mixed_block_threads(int mode, int nmax);
 // most Q points per CTA tile of a launch (quadrature order K)
-int mixed_tile_q(int mode, int nmax, int K);
+int mixed_tile_q(int mode, int nmax, int K, bool allow_pair = true);
 size_t mixed_dyn_smem(int mode, int nmax);
-cudaError_t mixed_occupancy(int mode, int nmax, int K, int *blocks_per_sm);
+cudaError_t mixed_occupancy(int mode, int nmax, int K, int *blocks_per_sm, bool allow_pair = true);
 cudaError_t launch_mixed(int mode, int nmax, int grid, const KernelArgs &a, const QuadConst &qc,
-                         cudaStream_t st);
+                         cudaStream_t st, bool allow_pair = true);
 bool mixed_bucket_ok(int mode, int nmax);
 
 // ---- paired kernel (nr_pair.cu): two evaluations per thread ----

@@ -829,9 +829,9 @@ bool mixed_bucket_ok(int mode, int nmax)
     return nmax == 0 || nmax == 1;
 }
 
-int mixed_tile_q(int mode, int nmax, int K)
+int mixed_tile_q(int mode, int nmax, int K, bool allow_pair)
 {
-    if (pair_eligible(mode, nmax, K)) {
+    if (allow_pair && pair_eligible(mode, nmax, K)) {
         const int slots = 2 * pair_block_threads(); // two evaluations per thread
         return std::min(slots / K, slots / kSubLanes);
     }
@@ -857,9 +857,9 @@ size_t mixed_dyn_smem(int mode, int nmax)
     return 0;
 }
 
-cudaError_t mixed_occupancy(int mode, int nmax, int K, int *blocks)
+cudaError_t mixed_occupancy(int mode, int nmax, int K, int *blocks, bool allow_pair)
 {
-    if (pair_eligible(mode, nmax, K)) return pair_occupancy(mode, nmax, K, blocks);
+    if (allow_pair && pair_eligible(mode, nmax, K)) return pair_occupancy(mode, nmax, K, blocks);
     switch (mode) {
     case kModel:
         return nmax == 1 ? occupancy_one<kModel, 1>(K, blocks) : occupancy_one<kModel, 0>(K, blocks);
@@ -879,10 +879,10 @@ cudaError_t mixed_occupancy(int mode, int nmax, int K, int *blocks)
 }
 
 cudaError_t launch_mixed(int mode, int nmax, int grid, const KernelArgs &a, const QuadConst &qc,
-                         cudaStream_t st)
+                         cudaStream_t st, bool allow_pair)
 {
     const int K = qc.K;
-    if (pair_eligible(mode, nmax, K)) return launch_pair(mode, nmax, grid, a, qc, st);
+    if (allow_pair && pair_eligible(mode, nmax, K)) return launch_pair(mode, nmax, grid, a, qc, st);
     switch (mode) {
     case kModel:
         return nmax == 1 ? launch_one<kModel, 1>(grid, K, a, qc, st) : launch_one<kModel, 0>(grid, K, a, qc, st);

@@ -635,3 +635,22 @@ def test_vi_step_parity_and_graph_replay():
     assert int(t2.item()) == t0 + 2
     smp.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("name,S", [("uneven", 40), ("thick_oxide", 64), ("oled_cofit", 6), ("film_1l", 48)])
+def test_autotuned_plan_keeps_parity(name, S):
+    """nr_plan with autotune = 1 times the candidate launch shapes (paired or
+    one-evaluation kernel, widest tile or half) per register bucket and keeps
+    the fastest; whatever it picks matches the oracle."""
+    wl = W.make_workload(name, n_stacks=S)
+    ctx = nr.Context(n_quad=wl.n_quad, autotune=True)
+    b = nr.Batch.from_workload(wl)
+    ctx.plan(b)
+    info = ctx.plan_info(b)
+    assert info["tile_q"] >= 1 and info["grid_ctas"] >= 1 and info["launches"] >= 1
+    gpu = {"m": ctx.reflectivity(b).cpu().numpy().astype(np.float64), "ll": ctx.loglik(b).cpu().numpy()}
+    ll, g = ctx.loglik_grad(b)
+    gpu["ll_g"], gpu["g"] = ll.cpu().numpy(), g.cpu().numpy()
+    gpu["flags"] = ctx.device_status()
+    ctx.close()
+    assert_parity(wl, gpu, run_oracle(wl))
