@@ -244,13 +244,45 @@ __device__ __forceinline__ c2 mobius2(c2 r, c2 Y, c2 &D)
     return cmul2(cadd2(r, Y), D);
 }
 
+// Drains `cnt` queued interior-edge entries of one warp (one per lane) into
+// the lane-pair partials of the rolled kernels (acc points at this lane
+// pair's slot of medium 1's Re partial; stride between partials `stride`,
+// Re -> Im distance `im_off`).  Lanes 2i and 2i+1 share a slot: the even
+// lanes add first, then the odd ones, so the order of the additions is
+// fixed.  Called by whole warps; kept out of line (rare path).
+template <int EQ, bool RES>
+__device__ __noinline__ float eq_drain_lanepair(float2 (*q)[EQ], const int *qj, const float4 *med, const float4 *lay,
+                                                int n, int lane, int cnt, float *acc, int stride, int im_off)
+{
+    float res = 0.f; // the resolution-mode term of the entry (factor in q[3])
+    const bool on = lane < cnt;
+    int j = 1;
+    float2 ub = make_float2(0.f, 0.f);
+    if (on) {
+        j = qj[lane];
+        ub = edge_entry_ubar(q[0][lane], q[1][lane], q[2][lane], j, n, med, lay);
+        if constexpr (RES) res = 2.f * ub.x * q[3][lane].x;
+    }
+    for (int parity = 0; parity < 2; ++parity) {
+        if (on && (lane & 1) == parity) {
+            // conj(kbar)/k_j = 2 conj(ubar)
+            acc[(j - 1) * stride] += 2.f * ub.x;
+            acc[(j - 1) * stride + im_off] += -2.f * ub.y;
+        }
+        __syncwarp();
+    }
+    return res;
+}
+
 // ---------------------------------------------------------------- traits --
 // STORE (1-2 layer gradients): unrolled sweeps, every forward intermediate
 // and the partial gradients in registers.  ROLL (the 4-20 layer buckets,
 // i.e. 3-20 layers): rolled sweeps
 // peeled at the first and last steps; X_j (both halves) and the partial
-// gradients (both halves summed, one float per thread) in shared memory;
-// k, r and E recomputed in the adjoint; edge entries keep the node k_0.
+// gradients in shared memory, the latter one float per lane pair (both
+// halves of lanes 2i and 2i+1 summed: half the storage, which lets the
+// 12-layer bucket run 4 CTAs per SM); k, r and E recomputed in the adjoint;
+// edge entries keep the node k_0.
 template <int MODE, int NMAX>
 struct PairTraits {
     static constexpr bool GRAD = MODE == kGrad || MODE == kGradRes;
@@ -261,7 +293,9 @@ struct PairTraits {
     static constexpr int NACC = 4 * NMAX + 3;
     static constexpr int MINB = !GRAD ? NR_PAIR_MINB_FWD : NMAX == 1 ? NR_PAIR_MINB1
                                 : NMAX == 2 ? NR_PAIR_MINB2 : NR_PAIR_MINB_DEEP;
-    static constexpr size_t DYN = ROLL ? (size_t)NACC * kPairBlock * 4 + (size_t)(NMAX + 1) * kPairBlock * 16 : 0;
+    // ROLL: partials per lane pair (kPairBlock / 2 floats per index), then X_j
+    static constexpr size_t DYN = ROLL ? (size_t)NACC * (kPairBlock / 2) * 4 + (size_t)(NMAX + 1) * kPairBlock * 16
+                                       : 0;
 };
 
 // ---------------------------------------------------------------- kernel --
@@ -292,7 +326,11 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
     static_assert(CAPQ >= 2 * BLOCK / kSubLanes, "a super-tile holds at least one tile");
 
     __shared__ StackSmem<NM> sm;
-    __shared__ __align__(16) float sh_wR[2][4 * BLOCK]; // w_k R per (Q slot, node), double-buffered
+    // w_k R per (Q slot, node), double-buffered.  TQ KP <= 4 BLOCK for any K >= 3;
+    // the rolled kernels, short of shared memory, take the exact maximum
+    // over K >= 3 (408 at K = 5: 51 Q points x 8)
+    constexpr int WRN = ROLL ? 416 : 4 * BLOCK;
+    __shared__ __align__(16) float sh_wR[2][WRN];
     __shared__ float4 sh_qd[CAPQ];                      // (Q/2, dQ/2, R_obs, 1/err) per staged Q point
     __shared__ float2 sh_rs[LIK ? CAPQ : 1];            // (residual, S) per staged Q point
     __shared__ double sh_red[WARPS][32];
@@ -302,10 +340,12 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
     __shared__ int sh_last;
     __shared__ float2 sh_eq[GRAD ? WARPS : 1][EQF][GRAD ? EQ : 1];
     __shared__ int sh_eqj[GRAD ? WARPS : 1][GRAD ? EQ : 1];
-    // ROLL: [NACC][BLOCK] partial gradients, then [NM+1][BLOCK] X_j pairs
+    // ROLL: [NACC][BLOCK/2] partial gradients (one float per lane pair), then
+    // [NM+1][BLOCK] X_j pairs
+    constexpr int HALF = BLOCK / 2;
     extern __shared__ __align__(16) float sh_dyn[];
     float *sh_acc = sh_dyn;
-    float4 *sh_X = reinterpret_cast<float4 *>(sh_dyn + (ROLL ? NACC * BLOCK : 0));
+    float4 *sh_X = reinterpret_cast<float4 *>(sh_dyn + (ROLL ? NACC * HALF : 0));
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -345,7 +385,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
     const int sgl = nslots <= 1 ? 32 : nslots <= 2 ? 16 : nslots <= 4 ? 8 : nslots <= 8 ? 4 : nslots <= 16 ? 2 : 1;
     const float g_max = fmaxf(fabsf(qc.g_hi[0]), fabsf(qc.g_hi[K - 1]));
 
-    for (int i = tid; i < 8 * BLOCK; i += BLOCK) (&sh_wR[0][0])[i] = 0.f; // padding stays 0
+    for (int i = tid; i < 2 * WRN; i += BLOCK) (&sh_wR[0][0])[i] = 0.f; // padding stays 0
 
     for (;;) {
         if (tid == 0) sh_item = atomicAdd(&ka.ticket[0], 1);
@@ -360,22 +400,28 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
 
         f2 accr[ROLL ? 1 : NACC];
         if constexpr (ROLL) {
-            for (int i = 0; i < NACC; ++i) sh_acc[i * BLOCK + tid] = 0.f;
+            for (int i = tid; i < NACC * HALF; i += BLOCK) sh_acc[i] = 0.f;
         } else {
 #pragma unroll
             for (int i = 0; i < NACC; ++i) accr[i] = bc(0.f);
         }
         constexpr int oD = 0, oUr = NM, oUi = 2 * NM + 1, oS = 3 * NM + 2;
+        // ROLL: the lane pair's partial idx += t (t: this lane's both halves);
+        // called by whole warps
+        auto acc_lanepair = [&](int idx, float t) __attribute__((always_inline)) {
+            t += __shfl_xor_sync(kFull, t, 1);
+            if (!(lane & 1)) sh_acc[idx * HALF + (tid >> 1)] += t;
+        };
         // partial gradient idx += v (both halves)
         auto acc_add = [&](int idx, f2 v) __attribute__((always_inline)) {
-            if constexpr (ROLL) sh_acc[idx * BLOCK + tid] += v.x + v.y;
+            if constexpr (ROLL) acc_lanepair(idx, v.x + v.y);
             else accr[idx] = padd(accr[idx], v);
         };
         // partial gradient idx += a b + c d
         auto acc_fma2 = [&](int idx, f2 a, f2 b, f2 c, f2 d) __attribute__((always_inline)) {
             if constexpr (ROLL) {
                 const f2 t = pfma(a, b, pmul(c, d));
-                sh_acc[idx * BLOCK + tid] += t.x + t.y;
+                acc_lanepair(idx, t.x + t.y);
             } else {
                 accr[idx] = pfma(a, b, pfma(c, d, accr[idx]));
             }
@@ -385,8 +431,9 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
         // drain `cnt` <= 32 queued entries, one per lane (scalar edge adjoint)
         auto eq_drain = [&](int cnt) {
             if constexpr (ROLL) {
-                const float r = eq_drain_smem<EQ, RES>(sh_eq[warp], sh_eqj[warp], sm.med, sm.lay, n, lane, cnt,
-                                                       sh_acc + oUr * BLOCK + tid, BLOCK, (oUi - oUr) * BLOCK);
+                const float r = eq_drain_lanepair<EQ, RES>(sh_eq[warp], sh_eqj[warp], sm.med, sm.lay, n, lane, cnt,
+                                                           sh_acc + oUr * HALF + (tid >> 1), HALF,
+                                                           (oUi - oUr) * HALF);
                 if constexpr (RES) gres_acc.x += r;
             } else if (lane < cnt) {
                 const int j = sh_eqj[warp][lane];
@@ -807,7 +854,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                                         : i < 2 * n + 1 ? NM + (i - n)
                                         : i < 3 * n + 2 ? 2 * NM + 1 + (i - 2 * n - 1)
                                                         : 3 * NM + 2 + (i - 3 * n - 2);
-                        float v = sh_acc[idx * BLOCK + tid];
+                        float v = tid < HALF ? sh_acc[idx * HALF + tid] : 0.f;
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
                         if (lane == 0) sh_red[warp][c] = (double)v;
