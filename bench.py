@@ -275,6 +275,8 @@ def run_reference(args):
                  probe.r_err, probe.n_quad)
     dt = time.perf_counter() - t0
     count = int(max(1, min(wl.n_stacks, probe.n_stacks * 0.1 / max(dt, 1e-6))))
+    # a whole number of stacks per thread, so that no core idles in a step
+    count = min(wl.n_stacks, max(threads, int(round(count / threads)) * threads))
     sub = wl.subset(np.arange(count))
 
     def step():
