@@ -115,9 +115,9 @@ FULL = [("thick_oxide", 64), ("film_1l", 48), ("oled_cofit", 12), ("uneven", 12)
 @pytest.mark.parametrize("name,samples", FULL)
 def test_mixed_parity_full_size_sampled(name, samples):
     wl = W.make_workload(name)
-    gpu = run_gpu(wl, modes=("grad",))
+    gpu = run_gpu(wl, modes=("loglik", "grad"))
     assert gpu["flags"] == 0
-    assert np.all(np.isfinite(gpu["g"])) and np.all(np.isfinite(gpu["ll_g"]))
+    assert np.all(np.isfinite(gpu["g"])) and np.all(np.isfinite(gpu["ll_g"])) and np.all(np.isfinite(gpu["ll"]))
     rng = np.random.default_rng(20250906)
     stacks = np.sort(rng.choice(wl.n_stacks, size=min(samples, wl.n_stacks), replace=False))
     sub = wl.subset(stacks)
@@ -126,6 +126,8 @@ def test_mixed_parity_full_size_sampled(name, samples):
     g = np.concatenate([gpu["g"][po[s]:po[s + 1]] for s in stacks])
     ll = gpu["ll_g"][stacks]
     assert np.max(np.abs(ll - ref["ll"]) / np.abs(ref["ll"])) <= TOL_LL
+    # the forward-only call (its own kernels) at the same stacks
+    assert np.max(np.abs(gpu["ll"][stacks] - ref["ll"]) / np.abs(ref["ll"])) <= TOL_LL
     assert grad_err(sub, g, ref["g"]) <= TOL_G
     # a property that holds for every stack: only SLD differences matter,
     # so d/d rho_0 = -sum_j d/d rho_j
