@@ -1,5 +1,9 @@
-// nr_mixed.cu -- the fast path: batched reflectivity, log-likelihood and its
-// exact gradient in complex FP32 with double-float guards, for sm_103a.
+// nr_mixed.cu -- batched reflectivity, log-likelihood and its exact gradient
+// in complex FP32 with double-float guards, for sm_103a, one evaluation per
+// thread.  The two-evaluations-per-thread kernels of nr_pair.cu run instead
+// wherever they apply (K >= 3, gradient buckets up to 20 layers, both forward
+// buckets); this kernel serves K < 3, the 32- and 64-layer gradient buckets,
+// and builds with NR_PAIR=0, and the autotuner may pick it per bucket.
 //
 // Work decomposition.  A work item is a range of Q points of one stack.  A
 // persistent CTA takes items from a queue (atomic ticket, cost-sorted on the
