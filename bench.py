@@ -2,29 +2,37 @@
 
 Metric: forward+gradient (sample x Q-node) evaluations per second, where one
 evaluation is one (stack, Q point, quadrature node) triple of a
-nr_loglik_grad call.  Workload (default): the thick-oxide film fit --
-16384 parameter samples of a 1-layer 1000-3000 A film on Si, 400 Q points in
-[0.005, 0.25] 1/A, dQ/Q = 3 % FWHM, 21 Gauss-Hermite nodes (137.6 M
-evaluations per step), data from the CPU oracle x lognormal 5 % noise.
+nr_loglik_grad call.  Workload (default): the VI/HMC gradient step --
+65536 reparameterised samples x 3 contrasts of a 12-layer stack (196608
+stacks), 300 Q points per contrast in [0.005, 0.3] 1/A, dQ/Q = 5 % FWHM,
+21 Gauss-Hermite nodes: 1.239 G evaluations per step, data from the CPU
+oracle x lognormal 5 % noise.
 
 One step = one nr_loglik_grad call over the whole batch (inputs resident in
-HBM).  Between timed steps L2 is flushed by writing a 512 MiB buffer; each
-step is timed with CUDA events on the launching stream.  `e2e` repeats the
-measurement through the C-ABI call with pinned HOST buffers (the library's
-H2D copies, compute and D2H copies inside the timed call).
+HBM), captured once as a CUDA graph and replayed.  Between timed steps L2 is
+flushed by writing a 512 MiB buffer; each step is timed with CUDA events on
+the launching stream.  `e2e` repeats the measurement through the C-ABI call
+with pinned HOST buffers (the library's H2D copies, compute and D2H copies
+inside the timed call).
+
+The roofline denominators are measured in the same run: throughput probes
+of the FP32 FMA (scalar and paired f32x2), FP64 FMA and ex2 pipes
+(libnr_peak.so), with the SM clock sampled while they run.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload NAME] [--no-cpu-baseline]
+                  [--workload NAME] [--scaling weak|strong] [--no-cpu-baseline]
 
 `--impl reference` times the plain CPU oracle on the host cores (there is
 no reference implementation of this method to run): a bounded sample of the
 same workload per step.  Under torchrun (N > 1) each rank runs its own
-seeded copy of the workload (weak scaling, no collective in the data path);
-rank 0 prints one JSON line.
+seeded copy of the workload (`--scaling weak`, the default) or a
+cost-balanced share of one batch (`--scaling strong`); no collective in the
+data path; rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -41,9 +49,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+grad (sample x Q-node) evals/s"
 UNIT = "evals/s"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
+DEFAULT_WORKLOAD = "vi_step"
+SECONDARY = ("thick_oxide", "oled_cofit", "uneven", "film_1l")
 
 
 def flops_per_eval(n: int, K: int) -> float:
@@ -69,8 +78,25 @@ def flops_per_eval(n: int, K: int) -> float:
     return float(fwd + seed + adj + per_q)
 
 
-def peak_fp32_tflops(mhz: float = SM_MAX_MHZ_NOMINAL) -> float:
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+def flops_per_eval_fwd(n: int, K: int) -> float:
+    """Algorithmic FP32 flops of one forward (log-likelihood) evaluation:
+    the forward sweep of flops_per_eval, the smearing product and sum (2),
+    and per Q point the model, the residual (4) and the likelihood terms
+    (15)."""
+    fwd = 15 + 6 + 10 + 29 + 3 + n * (25 + 34 + 18 + 6 + 20)
+    return float(fwd + 2 + 19.0 / K)
+
+
+def workload_flops(wl, per_eval) -> float:
+    """Sum over stacks of per_eval(n, K) x the stack's evaluations."""
+    oo = wl.out_off
+    return float(sum(per_eval(int(n), wl.n_quad) * (oo[s + 1] - oo[s]) * wl.n_quad
+                     for s, n in enumerate(wl.n_layers)))
+
+
+def sm_count(dev) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
 
 
 def _dist():
@@ -80,12 +106,17 @@ def _dist():
     return ws, rank, local
 
 
-def rank_workload(name: str, rank: int, n_stacks=None):
-    """Weak scaling: every rank evaluates its own seeded copy of the workload
-    (independent parameter samples, same datasets); no data moves between
-    ranks."""
+def rank_workload(name: str, rank: int, n_stacks=None, scaling: str = "weak", world: int = 1):
+    """The stacks rank `rank` evaluates.  weak: its own seeded copy of the
+    workload (independent parameter samples, same datasets); strong: its
+    cost-balanced share of the one batch (shard.workload_partition).  No
+    data moves between ranks either way."""
     from paper_2509_06924_gb300 import workloads as W
-    return W.make_workload(name, n_stacks=n_stacks, seed_offset=rank)
+    if scaling == "weak":
+        return W.make_workload(name, n_stacks=n_stacks, seed_offset=rank)
+    from paper_2509_06924_gb300 import shard
+    wl = W.make_workload(name, n_stacks=n_stacks)
+    return wl.subset(shard.workload_partition(wl, world)[rank])
 
 
 def max_over_ranks(value: float, device) -> float:
@@ -97,6 +128,67 @@ def max_over_ranks(value: float, device) -> float:
     t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def sum_over_ranks(value: float, device) -> float:
+    """Sum of a scalar over ranks (the evaluations of a strong-scaling split)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class PeakProbe:
+    """The arithmetic-pipe throughput probes of libnr_peak.so."""
+
+    KINDS = {"ffma": 0, "ffma2": 1, "dfma": 2, "ex2": 3}
+
+    def __init__(self):
+        from paper_2509_06924_gb300 import _build
+        self.lib = ctypes.CDLL(_build.build_peak())
+        self.lib.nr_peak_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        self.lib.nr_peak_run.restype = ctypes.c_int
+        self.lib.nr_peak_threads.restype = ctypes.c_int
+
+    def run(self, kind: str, out, ctas_per_sm: int, iters: int, reps: int):
+        ms, ops = ctypes.c_double(), ctypes.c_double()
+        rc = self.lib.nr_peak_run(self.KINDS[kind], ctas_per_sm, iters, reps, ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.byref(ms), ctypes.byref(ops))
+        if rc != 0:
+            raise RuntimeError(f"peak probe {kind} failed with code {rc}")
+        return ms.value, ops.value
+
+
+def measure_peaks(dev, seconds: float = 0.8) -> dict:
+    """Sustained throughput of each probe over about `seconds` of back-to-back
+    launches (8 CTAs of 256 threads per SM, 8 independent chains a thread),
+    with the SM clock sampled during the run; rates in ops/s (flops for the
+    FMA kinds) and per SM clock cycle."""
+    import torch
+    probe = PeakProbe()
+    sms = sm_count(dev)
+    ctas = 8
+    out = torch.empty(sms * ctas * probe.lib.nr_peak_threads(), dtype=torch.float32, device=dev)
+    res = {}
+    for kind in ("ffma", "ffma2", "dfma", "ex2"):
+        iters = 64 if kind == "dfma" else 256
+        ms, _ = probe.run(kind, out, ctas, iters, 2)              # calibrate
+        reps = max(3, int(seconds * 1e3 / max(ms / 2, 1e-3)))
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            ms, ops = probe.run(kind, out, ctas, iters, reps)
+        c = clk.summary()
+        rate = ops / (ms * 1e-3)
+        mhz = c["sm_mhz"] or SM_MAX_MHZ_NOMINAL
+        res[kind] = {"ops_per_s": rate, "ms": ms, "sm_mhz": c["sm_mhz"], "reasons": c["reasons"],
+                     "per_sm_per_clk": rate / (sms * mhz * 1e6)}
+    res["sms"] = sms
+    res["note"] = ("FMA kinds in flops (an FMA is 2, a paired f32x2 FMA 4), ex2 in results; "
+                   "per_sm_per_clk divides by the SM count and the median SM clock sampled during the probe")
+    return res
 
 
 class ClockSampler:
@@ -188,42 +280,69 @@ def profile_record(workload: str) -> dict:
     return rec if rec.get("kernel source sha256[:16]") == kernel_source_hash() else {}
 
 
-def fp64_fd_baseline(wl, stacks: int = 1024) -> dict:
+def fp64_fd_baseline(wl, stacks: int = 1024, reps: int = 2) -> dict:
     """The plain FP64 GPU path with central-difference gradients (2P + 1
-    forward evaluations per stack) on the first `stacks` stacks."""
+    forward evaluations per stack) on the first `stacks` stacks.  Also
+    returns its log-likelihoods and gradient (host arrays, key "_out") for
+    the accuracy check of the oracle leg."""
     import torch
     import paper_2509_06924_gb300 as nr
     sub = wl.subset(np.arange(min(stacks, wl.n_stacks)))
     ctx = nr.Context(n_quad=sub.n_quad, precision="fp64")
     b = nr.Batch.from_workload(sub)
     ctx.plan(b)
-    ctx.loglik_grad(b)
+    ll, g = ctx.loglik_grad(b)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    reps = 2
     for _ in range(reps):
-        ctx.loglik_grad(b)
+        ctx.loglik_grad(b, ll_out=ll, grad_out=g)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     # the plain FP64 forward alone (model, smearing and log-likelihood)
-    ctx.loglik(b)
+    ll2 = ctx.loglik(b)
     torch.cuda.synchronize()
     e0.record()
     for _ in range(reps):
-        ctx.loglik(b)
+        ctx.loglik(b, out=ll2)
     e1.record()
     torch.cuda.synchronize()
     ms_fwd = e0.elapsed_time(e1) / reps
+    out = (ll.cpu().numpy(), g.cpu().numpy())
     ctx.close()
+    n = int(sub.n_layers.max()) if sub.n_stacks else 0
     return {"value": sub.evals / (ms * 1e-3), "unit": UNIT, "sample": f"first {sub.n_stacks} stacks",
-            "ms_per_call": ms, "forward_value": sub.evals / (ms_fwd * 1e-3), "forward_ms_per_call": ms_fwd}
+            "ms_per_call": ms, "forward_value": sub.evals / (ms_fwd * 1e-3), "forward_ms_per_call": ms_fwd,
+            "forward_passes_per_eval": 2 * (4 * n + 6) + 1, "_out": out}
 
 
-def cpu_baseline(wl, target_s: float = 10.0) -> dict:
+def accuracy(wl, count: int, ll, g, m, ll_ref, g_ref, m_ref=None) -> dict:
+    """Worst errors over the first `count` stacks against the oracle: the
+    smeared model max |log m - log m_ref|, |l - l_ref| / |l_ref| and the
+    scaled gradient error max|(g - g_ref) typ| / max|g_ref typ| per stack
+    (typ: 1 A, 1e-6, 1e-8, 1 A, 1, 1e-7 per parameter class)."""
+    from paper_2509_06924_gb300 import workloads as W
+    po = wl.par_off
+    e_ll = float(np.max(np.abs(ll[:count] - ll_ref[:count]) / np.abs(ll_ref[:count]))) if count else 0.0
+    e_g = 0.0
+    for s in range(count):
+        typ = W.typical_scale(int(wl.n_layers[s]))
+        gs, rs = g[po[s]:po[s + 1]] * typ, g_ref[po[s]:po[s + 1]] * typ
+        e_g = max(e_g, float(np.max(np.abs(gs - rs)) / np.max(np.abs(rs))))
+    out = {"stacks": int(count), "loglik_rel": e_ll, "grad_scaled": e_g}
+    if m is not None and m_ref is not None:
+        k = int(wl.out_off[count])
+        out["log_model_abs"] = float(np.max(np.abs(np.log(m[:k].astype(np.float64)) - np.log(m_ref[:k]))))
+    return out
+
+
+def cpu_baseline(wl, target_s: float = 10.0, gpu=None, fd=None) -> dict:
     """The CPU oracle as it stands, on the host cores, on a bounded sample of
-    the workload's stacks (fwd + exact dual-number gradient)."""
+    the workload's stacks (fwd + exact dual-number gradient).  With `gpu`
+    (host arrays ll, g, m of the timed batch) and `fd` (the FP64 + central
+    difference path's ll, g on its first stacks), the oracle's results on the
+    sample also give the accuracy of both paths."""
     import oracle
     threads = oracle.max_threads()
     probe = max(1, min(wl.n_stacks, threads))
@@ -236,8 +355,8 @@ def cpu_baseline(wl, target_s: float = 10.0) -> dict:
     count = max(probe, count // threads * threads) if count >= threads else count
     sub = wl.subset(np.arange(count))
     t0 = time.perf_counter()
-    oracle.batch("grad", sub.n_layers, sub.params, sub.dataset, sub.q_off, sub.q, sub.dq, sub.r_obs, sub.r_err,
-                 sub.n_quad)
+    ll_ref, g_ref = oracle.batch("grad", sub.n_layers, sub.params, sub.dataset, sub.q_off, sub.q, sub.dq,
+                                 sub.r_obs, sub.r_err, sub.n_quad)
     dt = time.perf_counter() - t0
     out = {"value": sub.evals / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
            "sample": f"first {count} of {wl.n_stacks} stacks ({sub.evals} evals, {dt:.1f} s, fwd + dual-number grad)"}
@@ -255,6 +374,15 @@ def cpu_baseline(wl, target_s: float = 10.0) -> dict:
     dt1 = time.perf_counter() - t0
     out["value_1core"] = sub1.evals / dt1
     out["sample_1core"] = f"first {c1} stacks ({sub1.evals} evals, {dt1:.1f} s, one thread)"
+    if gpu is not None:
+        m_ref = oracle.batch("model", sub.n_layers, sub.params, sub.dataset, sub.q_off, sub.q, sub.dq, None, None,
+                             sub.n_quad)
+        acc = {"mixed": accuracy(wl, count, gpu["ll"], gpu["g"], gpu.get("m"), ll_ref, g_ref, m_ref),
+               "bounds": {"log_model_abs": 1e-5, "loglik_rel": 1e-5, "grad_scaled": 1e-4}}
+        if fd is not None:
+            k = min(count, fd[0].size)
+            acc["fp64_fd"] = accuracy(wl, k, fd[0], fd[1], None, ll_ref, g_ref)
+        out["_accuracy"] = acc
     return out
 
 
@@ -291,7 +419,7 @@ def run_reference(args):
     dt = (time.perf_counter() - t0) / args.steps
     value = sub.evals / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": args.scaling,
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "stacks_per_step": count, "q_points": int(wl.q_off[-1]),
                        "quad_nodes": wl.n_quad},
@@ -438,6 +566,63 @@ def vi_measure(nr, W, dev, restarts=100, iters=2000, lr=0.005, scale0=0.01, tail
     return out
 
 
+def vi_step_measure(nr, W, dev, restarts=65536, steps=5) -> dict:
+    """One variational-inference iteration (Secs. 2.4 and 4.2) for 65536
+    restarts of the 12-layer, 3-contrast co-fit at once -- 65536
+    reparameterised samples x 3 contrasts x 300 Q x 21 nodes of forward +
+    adjoint gradient of the summed log-likelihood, plus the draw, the
+    reparameterisation and the Adam update -- captured as one CUDA graph and
+    replayed with fresh normal draws each iteration."""
+    import torch
+    nl, ds, src, val, lo, hi, ut = W.cofit_sampler_model("vi_step")
+    wl = W.make_workload("vi_step", n_stacks=1)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    q, dq, ro, re = (torch.as_tensor(a, device=dev) for a in (wl.q, wl.dq, wl.r_obs, wl.r_err))
+    smp = nr.Sampler(ctx, restarts, nl, ds, wl.q_off, q, dq, ro, re, src, val, lo, hi)
+    P = ut.size
+    nphi = nr.vi_phi_size(P)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.SEED_BASE + 6)
+    phi = torch.zeros(restarts, nphi, dtype=torch.float64, device=dev)
+    phi[:, :P] = torch.as_tensor(ut, device=dev)[None, :] + 0.02 * torch.randn(
+        restarts, P, generator=gen, device=dev, dtype=torch.float64)
+    diag = torch.as_tensor([i * (i + 1) // 2 + i for i in range(P)], device=dev)
+    phi[:, P + diag] = float(np.log(0.01))
+    m = torch.zeros_like(phi)
+    v = torch.zeros_like(phi)
+    t = torch.zeros(1, dtype=torch.int32, device=dev)
+    eps = torch.empty(restarts, P, dtype=torch.float64, device=dev)
+    elbo = torch.empty(restarts, dtype=torch.float64, device=dev)
+    s = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(s):
+        eps.normal_(generator=gen)
+        smp.vi_step(phi, m, v, t, eps, lr=0.005, elbo_out=elbo, stream=s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        smp.vi_step(phi, m, v, t, eps, lr=0.005, elbo_out=elbo, stream=s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        eps.normal_(generator=gen)
+        graph.replay()
+        e0.record(s)
+        for _ in range(steps):
+            eps.normal_(generator=gen)
+            graph.replay()
+        e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    status = ctx.device_status()
+    evals = restarts * int(wl.q_off[-1]) * wl.n_quad
+    finite = bool(torch.isfinite(elbo).all().item())
+    out = {"restarts": restarts, "contrasts": 3, "layers": int(nl[0]), "free_params": int(P),
+           "phi_per_restart": int(nphi), "ms_per_iteration": ms, "evals_per_s": evals / (ms * 1e-3),
+           "graph": True, "iterations": steps, "elbo_finite": finite, "device_flags": status}
+    smp.close()
+    ctx.close()
+    return out
+
+
 def time_device(fn, steps: int, flush, stream) -> float:
     """Mean device time (ms) of fn() over `steps` calls, L2 flushed before
     each, CUDA events on the launching stream; 3 warm-up calls first."""
@@ -456,6 +641,39 @@ def time_device(fn, steps: int, flush, stream) -> float:
     return sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / steps
 
 
+def measure_config(nr, W, name: str, dev, flush, stream, peak_flops: float, steps: int = 10) -> dict:
+    """fwd+grad and forward (log-likelihood) throughput of another workload,
+    each call timed like the headline step (L2 flushed, CUDA events), with
+    its flop-count fraction of the measured FP32 peak.  The one-layer film
+    (the plain-FP64-forward workload) also times the FP64 forward."""
+    import torch
+    wl = W.make_workload(name)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    b = nr.Batch.from_workload(wl, device=dev)
+    ctx.plan(b)
+    info = ctx.plan_info(b)
+    ll = torch.empty(wl.n_stacks, dtype=torch.float64, device=dev)
+    g = torch.empty(b.params.numel(), dtype=torch.float64, device=dev)
+    ms_g = time_device(lambda: ctx.loglik_grad(b, ll_out=ll, grad_out=g, stream=stream), steps, flush, stream)
+    ms_f = time_device(lambda: ctx.loglik(b, out=ll, stream=stream), steps, flush, stream)
+    status = ctx.device_status()
+    ctx.close()
+    fl_g, fl_f = workload_flops(wl, flops_per_eval), workload_flops(wl, flops_per_eval_fwd)
+    out = {"stacks": wl.n_stacks, "evals_per_call": wl.evals, "layers": sorted(set(int(x) for x in wl.n_layers)),
+           "fwd_grad": {"value": wl.evals / (ms_g * 1e-3), "ms_per_call": ms_g,
+                        "frac": fl_g / (ms_g * 1e-3) / peak_flops},
+           "loglik": {"value": wl.evals / (ms_f * 1e-3), "ms_per_call": ms_f,
+                      "frac": fl_f / (ms_f * 1e-3) / peak_flops},
+           "launches_per_call": info["launches"], "steps": steps, "device_flags": status}
+    if name == "film_1l":
+        c64 = nr.Context(n_quad=wl.n_quad, precision="fp64")
+        c64.plan(b)
+        ms64 = time_device(lambda: c64.loglik(b, out=ll, stream=stream), steps, flush, stream)
+        c64.close()
+        out["fp64_plain_loglik"] = {"value": wl.evals / (ms64 * 1e-3), "ms_per_call": ms64}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -470,8 +688,14 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
+    if args.no_peaks:   # profiling runs: the nominal FP32 rate stands in
+        nominal = sm_count(dev) * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6
+        peaks = {k: {"ops_per_s": nominal, "sm_mhz": None, "per_sm_per_clk": 256.0} for k in ("ffma", "ffma2")}
+    else:
+        peaks = measure_peaks(dev)
+    peak_fp32 = max(peaks["ffma"]["ops_per_s"], peaks["ffma2"]["ops_per_s"])
 
-    wl = rank_workload(args.workload, rank, args.stacks)
+    wl = rank_workload(args.workload, rank, args.stacks, args.scaling, ws)
     ctx = nr.Context(n_quad=wl.n_quad)
     batch = nr.Batch.from_workload(wl, device=dev)
     ctx.plan(batch)
@@ -479,16 +703,21 @@ def run_ours(args):
     ll = torch.empty(wl.n_stacks, dtype=torch.float64, device=dev)
     g = torch.empty(batch.params.numel(), dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)
 
-    def step():
-        ctx.loglik_grad(batch, ll_out=ll, grad_out=g, stream=stream)
-
-    for _ in range(max(args.warmup, 3)):
-        step()
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            ctx.loglik_grad(batch, ll_out=ll, grad_out=g, stream=stream)
     torch.cuda.synchronize()
     if ctx.device_status() != 0:
         raise RuntimeError("device status flags raised during warm-up")
+    # the step: one nr_loglik_grad call, captured once and replayed
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        ctx.loglik_grad(batch, ll_out=ll, grad_out=g, stream=stream)
+    with torch.cuda.stream(stream):
+        graph.replay()
+    torch.cuda.synchronize()
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -497,20 +726,25 @@ def run_ours(args):
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
         t_wall = time.perf_counter()
-        for i in range(args.steps):
-            flush.fill_(float(i))           # L2 flush outside the timed events
-            starts[i].record(stream)
-            step()
-            ends[i].record(stream)
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(float(i))           # L2 flush outside the timed events
+                starts[i].record(stream)
+                graph.replay()
+                ends[i].record(stream)
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     if ws > 1:
         dist.barrier()
     per_step = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(per_step) / len(per_step)
-    ms = max_over_ranks(ms, dev)
+    ms_rank = sum(per_step) / len(per_step)
+    ms = max_over_ranks(ms_rank, dev)
     evals = wl.evals
-    value = ws * evals / (ms * 1e-3)
+    if args.scaling == "weak":
+        total_evals = ws * evals
+    else:
+        total_evals = int(sum_over_ranks(float(evals), dev))
+    value = total_evals / (ms * 1e-3)
 
     # e2e: the same call with pinned host buffers (H2D + compute + D2H inside)
     e2e = None
@@ -520,29 +754,37 @@ def run_ours(args):
         hg = torch.empty(hbatch.params.numel(), dtype=torch.float64).pin_memory()
         for _ in range(3):
             ctx.loglik_grad(hbatch, ll_out=hll, grad_out=hg)
-        e2e_steps = max(5, min(args.steps, 50))
+        e2e_steps = max(3, min(args.steps, 20))
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             ctx.loglik_grad(hbatch, ll_out=hll, grad_out=hg)
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
         h2d = wl.params.nbytes + wl.q.nbytes + wl.dq.nbytes + wl.r_obs.nbytes + wl.r_err.nbytes
         d2h = hll.numel() * 8 + hg.numel() * 8
-        e2e = {"value": ws * wl.evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+        e2e = {"value": total_evals / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
 
     # forward-only paths on the same batch: the log-likelihood (model, smearing
     # and likelihood, no adjoint) and the smeared model alone
     fwd = None
+    m_out = torch.empty(batch.total_out, dtype=torch.float32, device=dev)
     if not args.no_forward:
-        m_out = torch.empty(batch.total_out, dtype=torch.float32, device=dev)
-        n_fwd = max(5, min(args.steps, 50))
-        ms_ll = max_over_ranks(time_device(lambda: ctx.loglik(batch, out=ll, stream=stream), n_fwd, flush,
+        ll_f = torch.empty_like(ll)
+        n_fwd = max(5, min(args.steps, 30))
+        ms_ll = max_over_ranks(time_device(lambda: ctx.loglik(batch, out=ll_f, stream=stream), n_fwd, flush,
                                            stream), dev)
         ms_r = max_over_ranks(time_device(lambda: ctx.reflectivity(batch, out=m_out, stream=stream), n_fwd,
                                           flush, stream), dev)
-        fwd = {"loglik": {"value": ws * evals / (ms_ll * 1e-3), "unit": UNIT, "ms_per_call": ms_ll},
-               "reflectivity": {"value": ws * evals / (ms_r * 1e-3), "unit": UNIT, "ms_per_call": ms_r},
+        fflops = workload_flops(wl, flops_per_eval_fwd)
+        fwd = {"loglik": {"value": total_evals / (ms_ll * 1e-3), "unit": UNIT, "ms_per_call": ms_ll,
+                          "roofline": {"bound": "alu", "achieved": fflops / (ms_ll * 1e-3) / 1e12,
+                                       "peak": peak_fp32 / 1e12, "unit": "TFLOP/s",
+                                       "frac": fflops / (ms_ll * 1e-3) / peak_fp32,
+                                       "flops_per_eval": fflops / evals}},
+               "reflectivity": {"value": total_evals / (ms_r * 1e-3), "unit": UNIT, "ms_per_call": ms_r},
                "steps": n_fwd}
+    else:
+        ctx.reflectivity(batch, out=m_out, stream=stream)
 
     status = ctx.device_status()
     if status != 0:
@@ -552,49 +794,65 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    flops = sum(flops_per_eval(int(n), wl.n_quad) * (wl.out_off[s + 1] - wl.out_off[s]) * wl.n_quad
-                for s, n in enumerate(wl.n_layers))
+    flops = workload_flops(wl, flops_per_eval)
     # layer-evaluations weight each evaluation by its interface count n + 1
     layer_evals = sum((int(n) + 1) * (wl.out_off[s + 1] - wl.out_off[s]) * wl.n_quad
                       for s, n in enumerate(wl.n_layers))
-    kernel_ms = ms  # the step is one launch of the gradient kernel per layer bucket
-    achieved = flops / (kernel_ms * 1e-3) / 1e12
-    peak = peak_fp32_tflops()
+    kernel_ms = ms_rank  # the step is one launch of the gradient kernel per layer bucket
+    achieved = flops / (kernel_ms * 1e-3)
     prof = profile_record(args.workload)
     traffic = float(prof["dram bytes per full launch"]) if "dram bytes per full launch" in prof else None
+    pk_kind = "ffma2" if peaks["ffma2"]["ops_per_s"] >= peaks["ffma"]["ops_per_s"] else "ffma"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None,
         "dtype": "f32 (double-float guards, f64 reductions)", "data": "synthetic",
         "config": {"workload": args.workload, "stacks": wl.n_stacks, "q_points": int(wl.q_off[-1]),
                    "quad_nodes": wl.n_quad, "layers": sorted(set(int(x) for x in wl.n_layers))[:4],
-                   "evals_per_step": evals, "l2": "flushed between steps (512 MiB write)",
-                   "launch": info},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "peak_basis": "FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)"},
+                   "evals_per_step": evals, "graph": "the step is one captured nr_loglik_grad call, replayed",
+                   "l2": "flushed between steps (512 MiB write)", "launch": info},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_fp32 / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / peak_fp32, "traffic": traffic,
+                     "flops_per_eval": flops / evals,
+                     "peak_basis": f"measured in this run: {pk_kind} probe (libnr_peak.so), "
+                                   f"{peaks[pk_kind]['per_sm_per_clk']:.1f} flop/SM/clk at a median "
+                                   f"{peaks[pk_kind]['sm_mhz']} MHz; nominal 152 SMs x 128 lanes x 2 flop "
+                                   f"x 2070 MHz = {152 * 128 * 2 * 2.07e-3:.1f} TFLOP/s"},
+        "peaks": peaks,
         "e2e": e2e,
-        "layer_evals_per_s": ws * layer_evals / (ms * 1e-3),
+        "layer_evals_per_s": layer_evals * (ws if args.scaling == "weak" else 1) / (ms * 1e-3),
         "forward": fwd,
-        "fp64_fd_baseline": None if args.no_cpu_baseline else fp64_fd_baseline(wl),
         "gpu_launches": int(info["launches"]) * args.steps,
         "clocks": clk.summary(),
         "wall_s_timed_region": t_wall,
     }
-    if line["fp64_fd_baseline"]:
-        line["fp64_fd_baseline"]["speedup"] = value / ws / line["fp64_fd_baseline"]["value"]
+    fd = None
+    if not args.no_cpu_baseline:
+        fd_stacks = 192 if args.workload in ("vi_step", "oled_cofit", "uneven") else 1024
+        fdb = fp64_fd_baseline(wl, stacks=fd_stacks)
+        fd = fdb.pop("_out")
+        fdb["speedup"] = value / ws / fdb["value"] if args.scaling == "weak" else value / fdb["value"]
+        line["fp64_fd_baseline"] = fdb
     if "fp32 lane ops per eval" in prof:
         ope = float(prof["fp32 lane ops per eval"])
-        peak_ops = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-        line["fp32_issue"] = {"ops_per_eval": ope, "achieved": value / ws * ope / 1e12, "peak": peak_ops,
-                              "unit": "T lane-ops/s", "frac": value / ws * ope / 1e12 / peak_ops,
+        lane_peak = max(peaks["ffma"]["ops_per_s"] / 2, peaks["ffma2"]["ops_per_s"] / 2)
+        line["fp32_issue"] = {"ops_per_eval": ope, "achieved": evals / (kernel_ms * 1e-3) * ope / 1e12,
+                              "peak": lane_peak / 1e12, "unit": "T lane-ops/s",
+                              "frac": evals / (kernel_ms * 1e-3) * ope / lane_peak,
                               "basis": "FP32 lane operations per evaluation counted by ncu (FFMA/FADD/FMUL, "
-                                       "paired FFMA2/FADD2/FMUL2 counted twice)"}
+                                       "paired FFMA2/FADD2/FMUL2 counted twice) over the measured FMA lane rate"}
     if ws == 1 and not args.no_infer:
+        line["secondary"] = {nm: measure_config(nr, W, nm, dev, flush, stream, peak_fp32)
+                             for nm in SECONDARY if nm != args.workload}
         line["hmc"] = hmc_measure(nr, W, dev)
         line["vi"] = vi_measure(nr, W, dev)
+        line["vi_step_graph"] = vi_step_measure(nr, W, dev)
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl)
+        torch.cuda.synchronize()
+        gpu = {"ll": ll.cpu().numpy(), "g": g.cpu().numpy(), "m": m_out.cpu().numpy()}
+        cb = cpu_baseline(wl, gpu=gpu, fd=fd)
+        line["accuracy"] = cb.pop("_accuracy")
+        line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -604,15 +862,20 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="thick_oxide")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--scaling", choices=["weak", "strong"], default="weak",
+                    help="N > 1: every rank its own copy of the workload (weak) or a cost-balanced share of one "
+                         "batch (strong)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement (profiling runs)")
     ap.add_argument("--no-forward", action="store_true", help="skip the forward-only timings (profiling runs)")
     ap.add_argument("--no-infer", action="store_true",
-                    help="skip the on-device HMC transition and VI run (profiling runs)")
+                    help="skip the other workloads, the on-device HMC transition and the VI runs (profiling runs)")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the pipe-throughput probes; the nominal FP32 rate stands in (profiling runs)")
     ap.add_argument("--stacks", type=int, default=None,
                     help="override the stack count (small profiling cases; not a bench line)")
     args = ap.parse_args()

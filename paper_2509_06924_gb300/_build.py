@@ -1,6 +1,8 @@
 """Builds the C-ABI library ``_build/libnr.so`` in-tree for sm_103a with
 nvcc (kernels) and g++ (host API), compiling the translation units in
-parallel.  No CMake, no torch extension machinery."""
+parallel, and the arithmetic-pipe probes ``_build/libnr_peak.so`` that the
+benchmark measures its roofline denominators with.  No CMake, no torch
+extension machinery."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -13,6 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libnr.so")
+PEAK_LIB = os.path.join(OUT_DIR, "libnr_peak.so")
+PEAK_SOURCE = "nr_peak.cu"
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["nr_mixed.cu", "nr_pair.cu", "nr_fp64.cu", "nr_noalloc.cu", "nr_profile.cu", "nr_hmc.cu", "nr_vi.cu"]
@@ -87,6 +91,20 @@ def build(force: bool = False, verbose: bool = False, defines=None, out: str | N
     _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"])
     os.replace(tmp, lib_path)
     return lib_path
+
+
+def build_peak(force: bool = False) -> str:
+    """Compile (if needed) and return the path of libnr_peak.so."""
+    src = os.path.join(CSRC, PEAK_SOURCE)
+    if not force and os.path.exists(PEAK_LIB) and os.path.getmtime(PEAK_LIB) >= max(
+            os.path.getmtime(src), os.path.getmtime(os.path.abspath(__file__))):
+        return PEAK_LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    tmp = PEAK_LIB + ".tmp"
+    _run([_nvcc(), "-std=c++17", *ARCH, "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-shared", src, "-o", tmp,
+          "-cudart", "static"])
+    os.replace(tmp, PEAK_LIB)
+    return PEAK_LIB
 
 
 if __name__ == "__main__":

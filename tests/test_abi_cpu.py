@@ -147,7 +147,22 @@ def test_flop_table_is_monotone_and_positive():
     assert all(b > a for a, b in zip(f, f[1:]))
     # the 1-layer count, term by term: forward 166, seed 11, adjoint 156
     assert abs(bench.flops_per_eval(1, 21) - (166 + 11 + 156 + 15 / 21)) < 1e-9
-    assert abs(bench.peak_fp32_tflops() - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+    # the forward count is the gradient's forward sweep plus smearing and
+    # likelihood terms, and below the fwd+grad count at every depth
+    assert abs(bench.flops_per_eval_fwd(1, 21) - (166 + 2 + 19 / 21)) < 1e-9
+    assert all(bench.flops_per_eval_fwd(n, 21) < bench.flops_per_eval(n, 21) for n in range(0, 21))
+
+
+def test_peak_probe_library_builds_and_exports():
+    from paper_2509_06924_gb300 import _build
+    lib = ctypes.CDLL(_build.build_peak())
+    assert lib.nr_peak_threads() == 256
+    # bad arguments are refused before any device call
+    ms, ops = ctypes.c_double(), ctypes.c_double()
+    lib.nr_peak_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    assert lib.nr_peak_run(7, 1, 1, 1, None, ctypes.byref(ms), ctypes.byref(ops)) == -1
+    assert lib.nr_peak_run(0, 0, 1, 1, None, ctypes.byref(ms), ctypes.byref(ops)) == -1
 
 
 def test_profile_record_reads_the_summary_format(tmp_path, monkeypatch):
