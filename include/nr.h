@@ -95,7 +95,10 @@ typedef struct nr_options {
     int32_t tile_q;        /* override: Q points per CTA tile (0 = auto)      */
     int32_t chunk_q;       /* override: Q points per work item (0 = auto)     */
     int32_t grid_ctas;     /* override: persistent CTAs (0 = auto)            */
-    int32_t reserved;
+    int32_t serial;        /* 1: launch the register buckets of a batch one
+                              after another on the call's stream; 0 (default):
+                              concurrently on forked streams joined back into
+                              it (each bucket is one persistent launch)      */
 } nr_options;
 
 typedef struct nr_batch {
@@ -202,6 +205,43 @@ nr_status nr_quadrature(int32_t K, double *x, double *w);
 nr_status nr_plan_info(nr_ctx *ctx, const nr_batch *batch, int64_t *evals, int32_t *tile_q,
                        int32_t *chunk_q, int32_t *grid_ctas, int32_t *launches);
 
+/* The launches one compute call makes on this batch after planning (and
+ * tuning), one per register bucket: grad = 1 the gradient calls, 0 the
+ * forward ones (model, log-likelihood).  *count receives the number of
+ * buckets; for i < min(*count, max_groups): nmax[i] the bucket's layer
+ * capacity (1: exactly one layer; 0: any, forward), paired[i] 1 when the
+ * two-evaluations-per-thread kernel runs it, tile_q[i] Q points per CTA
+ * tile, grid[i] persistent CTAs, items[i] work items.  Arrays may be NULL. */
+nr_status nr_plan_groups(nr_ctx *ctx, const nr_batch *batch, int32_t grad, int32_t max_groups, int32_t *count,
+                         int32_t *nmax, int32_t *paired, int32_t *tile_q, int32_t *grid, int32_t *items);
+
+/* ------------------------------------------------------------------------
+ * Autotune cache.  nr_plan on a context created with autotune = 1 times the
+ * candidate launch shapes of every register bucket (paired or one-evaluation
+ * kernel x tile of TQ or TQ/2 Q points x CTAs per SM at the occupancy limit,
+ * one fewer, or half) on the batch's own data and keeps the fastest.  When
+ * the environment variable NR_TUNE_CACHE names a file, the choices are read
+ * from it first and the new ones written back (a JSON object
+ * {"version": 1, "entries": {key: {"paired", "tile_q", "ctas_per_sm",
+ * "ms"}}}), so later processes skip the timing.  Key of an entry:
+ *   "<GPU name>|<SMs>|<mode>|<K>|<bucket nmax>|<log2 of the work items>|t<tuner version>"
+ * with mode 0 for the forward and 2 for the gradient launches.  The two
+ * calls below read and write one entry of such a file; they are host-only
+ * (no device needed).  _get returns NR_EINVAL when the file or the key is
+ * absent or unreadable; _put rewrites the file (keys may not contain '"'
+ * or '\'), NR_EINVAL on an I/O error.
+ * ---------------------------------------------------------------------- */
+typedef struct nr_tune_entry {
+    int32_t paired;      /* 1: the two-evaluations-per-thread kernel          */
+    int32_t tile_q;      /* Q points per CTA tile                              */
+    int32_t ctas_per_sm; /* persistent CTAs per SM                             */
+    int32_t reserved;
+    double ms;           /* time of the chosen shape's launch when tuned (ms) */
+} nr_tune_entry;
+
+nr_status nr_tune_cache_get(const char *path, const char *key, nr_tune_entry *entry);
+nr_status nr_tune_cache_put(const char *path, const char *key, const nr_tune_entry *entry);
+
 /* ------------------------------------------------------------------------
  * nr_loglik_grad_noalloc -- log-likelihood and gradient without allocating.
  * The paper has no counterpart: this entry point exists for callers that are
@@ -220,12 +260,17 @@ nr_status nr_plan_info(nr_ctx *ctx, const nr_batch *batch, int64_t *evals, int32
  *   loglik, grad: device outputs as for nr_loglik_grad (either may be NULL).
  *   device_flags: optional device int32; cleared, then given the NR_FLAG_*
  *                 bits this call raised (NULL: flags are not reported).
- *   stream:       cudaStream_t; the call is asynchronous on it.
+ *   stream:       cudaStream_t.  The work list is copied from pageable
+ *                 host memory of the library, so the call waits for the
+ *                 stream's earlier work before that copy and returns once
+ *                 it is staged; the kernels then run asynchronously.
  * Returns NR_EINVAL (with a message in nr_last_error) for more than
- * NR_NOALLOC_MAX_STACKS stacks, host-memory batches or bad metadata,
- * NR_ECUDA if a runtime call fails.
+ * NR_NOALLOC_MAX_STACKS stacks, host-memory batches, bad metadata or a
+ * stream that is capturing a CUDA graph (this entry point cannot be
+ * captured: a replay would copy whatever work list the latest call left in
+ * the library's host arrays), NR_ECUDA if a runtime call fails.
  * The first call on a device looks up the array's device address with that
- * device current; make it before any stream capture.  Every call shares the
+ * device current.  Every call shares the
  * one array and leaves its contents behind (the call clears what must start
  * at zero), so calls that overlap on the GPU (e.g. on two streams) race:
  * issue them on one stream.  Results equal nr_loglik_grad's up to rounding
@@ -331,6 +376,15 @@ typedef struct nr_adam {
 
 nr_status nr_vi_step(nr_sampler *sampler, double *phi, double *adam_m, double *adam_v, int32_t *t,
                      const double *eps, const nr_adam *opt, double *elbo, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Testing hook (the paper has no counterpart): the next `count` device
+ * allocations the library attempts (context status word, plans, work lists,
+ * staging buffers, sampler workspaces) fail as if the device were out of
+ * memory, without calling cudaMalloc; the call that needed one returns
+ * NR_ENOMEM and leaves the context usable.  0 disarms.  Process-wide.
+ * ---------------------------------------------------------------------- */
+nr_status nr_debug_fail_allocs(int32_t count);
 
 #ifdef __cplusplus
 }

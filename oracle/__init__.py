@@ -185,3 +185,42 @@ def batch(mode: str, n_layers, params, dataset, q_off, Q, dQ, Robs, err, K: int,
     if mode == "grad_res":
         return ll[:S], g, m[:S]
     return ll[:S], g
+
+
+def perturbation_floor(n_layers, params, dataset, q_off, Q, dQ, Robs, err, K: int, typ, n_pert: int = 3,
+                       seed: int = 0x5EED, n_threads: int = 0) -> dict:
+    """How far the exact results of each stack move when every input
+    parameter is perturbed by at most one FP32 unit roundoff: p_t = p (1 +
+    2^-24 u_t), u_t uniform in [-1, 1] per parameter, t = 1..n_pert.  Per
+    stack, the largest over t of
+      'loglik': |l_t - l| / |l|,
+      'model':  max_i |log m_t,i - log m_i| (the smeared model),
+      'grad':   ||(g_t - g) typ||_inf / ||g typ||_inf,
+    with typ packed like params.  An evaluation in FP32 arithmetic cannot be
+    expected to land closer to the exact result than this response: its own
+    roundings act as perturbations of the same size.  Condition estimate
+    for the parity bounds; not part of the method."""
+    nl = np.ascontiguousarray(n_layers, dtype=np.int32)
+    p = _f64(params)
+    typ = _f64(typ)
+    S = nl.size
+    po = np.concatenate([[0], np.cumsum(4 * nl.astype(np.int64) + 6)])
+    lens = (np.asarray(q_off)[1:] - np.asarray(q_off)[:-1])[np.asarray(dataset)]
+    oo = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    ll0, g0 = batch("grad", nl, p, dataset, q_off, Q, dQ, Robs, err, K, n_threads=n_threads)
+    m0 = batch("model", nl, p, dataset, q_off, Q, dQ, None, None, K, n_threads=n_threads)
+    rng = np.random.default_rng(seed)
+    f_ll, f_m, f_g = np.zeros(S), np.zeros(S), np.zeros(S)
+    for _ in range(n_pert):
+        pt = p * (1.0 + 2.0 ** -24 * rng.uniform(-1.0, 1.0, p.size))
+        ll, g = batch("grad", nl, pt, dataset, q_off, Q, dQ, Robs, err, K, n_threads=n_threads)
+        m = batch("model", nl, pt, dataset, q_off, Q, dQ, None, None, K, n_threads=n_threads)
+        for s in range(S):
+            f_ll[s] = max(f_ll[s], abs(ll[s] - ll0[s]) / abs(ll0[s]))
+            a, b = po[s], po[s + 1]
+            den = np.max(np.abs(g0[a:b] * typ[a:b]))
+            if den > 0:
+                f_g[s] = max(f_g[s], float(np.max(np.abs((g[a:b] - g0[a:b]) * typ[a:b])) / den))
+            if oo[s + 1] > oo[s]:
+                f_m[s] = max(f_m[s], float(np.max(np.abs(np.log(m[oo[s]:oo[s + 1]]) - np.log(m0[oo[s]:oo[s + 1]])))))
+    return {"loglik": f_ll, "model": f_m, "grad": f_g}

@@ -35,7 +35,8 @@ MAX_QUAD = 32
 EXPORTS = ("nr_create", "nr_destroy", "nr_last_error", "nr_plan", "nr_reflectivity", "nr_loglik",
            "nr_loglik_grad", "nr_loglik_grad_res", "nr_sld_profile", "nr_device_status", "nr_quadrature",
            "nr_plan_info", "nr_loglik_grad_noalloc", "nr_sampler_create", "nr_sampler_destroy",
-           "nr_sampler_logp_grad", "nr_hmc_step", "nr_vi_step")
+           "nr_sampler_logp_grad", "nr_hmc_step", "nr_vi_step", "nr_plan_groups", "nr_tune_cache_get",
+           "nr_tune_cache_put", "nr_debug_fail_allocs")
 NOALLOC_MAX_STACKS = 16384
 
 
@@ -49,7 +50,7 @@ class Options(ctypes.Structure):
     _fields_ = [("n_quad", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("deterministic", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("tile_q", ctypes.c_int32), ("chunk_q", ctypes.c_int32),
-                ("grid_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("grid_ctas", ctypes.c_int32), ("serial", ctypes.c_int32)]
 
 
 class CBatch(ctypes.Structure):
@@ -66,6 +67,11 @@ class CCofitModel(ctypes.Structure):
                 ("q_off", ctypes.c_void_p), ("q", ctypes.c_void_p), ("dq", ctypes.c_void_p),
                 ("r_obs", ctypes.c_void_p), ("r_err", ctypes.c_void_p), ("slot_src", ctypes.c_void_p),
                 ("slot_val", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("paired", ctypes.c_int32), ("tile_q", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("ms", ctypes.c_double)]
 
 
 class CAdam(ctypes.Structure):
@@ -116,6 +122,11 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             lib.nr_sampler_logp_grad.argtypes = [vp, vp, vp, vp, vp]
             lib.nr_hmc_step.argtypes = [vp, vp, vp, vp, vp, ctypes.c_double, i32, vp, vp, vp]
             lib.nr_vi_step.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.POINTER(CAdam), vp, vp]
+            lib.nr_plan_groups.argtypes = [vp, ctypes.POINTER(CBatch), i32, i32, i32p, i32p, i32p, i32p, i32p,
+                                           i32p]
+            lib.nr_tune_cache_get.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(TuneEntry)]
+            lib.nr_tune_cache_put.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(TuneEntry)]
+            lib.nr_debug_fail_allocs.argtypes = [i32]
             for name in EXPORTS:
                 if name not in ("nr_destroy", "nr_last_error", "nr_sampler_destroy"):
                     getattr(lib, name).restype = ctypes.c_int
@@ -220,13 +231,13 @@ class Context:
     current CUDA device."""
 
     def __init__(self, n_quad: int = 17, precision: str = "mixed", autotune: bool = False, tile_q: int = 0,
-                 chunk_q: int = 0, grid_ctas: int = 0):
+                 chunk_q: int = 0, grid_ctas: int = 0, serial: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2509_06924_gb300 needs a CUDA device (no CPU fallback)")
         self._lib = load_library()
         prec = {"mixed": NR_MIXED, "fp64": NR_FP64_PLAIN}[precision]
-        opt = Options(n_quad, prec, 1, int(autotune), tile_q, chunk_q, grid_ctas, 0)
+        opt = Options(n_quad, prec, 1, int(autotune), tile_q, chunk_q, grid_ctas, int(serial))
         h = ctypes.c_void_p()
         _check(self._lib.nr_create(ctypes.byref(h), ctypes.byref(opt)))
         self._h = h
@@ -257,6 +268,19 @@ class Context:
                                       ctypes.byref(cq), ctypes.byref(gr), ctypes.byref(la)))
         return {"evals": ev.value, "tile_q": tq.value, "chunk_q": cq.value, "grid_ctas": gr.value,
                 "launches": la.value}
+
+    def plan_groups(self, batch: Batch, grad: bool = True) -> list:
+        """The launches of one compute call on this batch (one per register
+        bucket): layer capacity, paired kernel or not, tile, grid, items."""
+        cb = batch._c()
+        cnt = ctypes.c_int32()
+        _check(self._lib.nr_plan_groups(self._h, ctypes.byref(cb), int(grad), 0, ctypes.byref(cnt), None, None,
+                                        None, None, None))
+        n = cnt.value
+        arrs = [(ctypes.c_int32 * max(n, 1))() for _ in range(5)]
+        _check(self._lib.nr_plan_groups(self._h, ctypes.byref(cb), int(grad), n, ctypes.byref(cnt), *arrs))
+        keys = ("nmax", "paired", "tile_q", "grid", "items")
+        return [{k: int(a[i]) for k, a in zip(keys, arrs)} for i in range(n)]
 
     def _alloc(self, batch: Batch, n, dtype, out=None):
         import torch
@@ -413,6 +437,26 @@ class Sampler:
         return elbo
 
 
+def tune_cache_get(path: str, key: str):
+    """One entry of an autotune cache file (dict), or None when absent."""
+    e = TuneEntry()
+    if load_library().nr_tune_cache_get(path.encode(), key.encode(), ctypes.byref(e)) != NR_OK:
+        return None
+    return {"paired": e.paired, "tile_q": e.tile_q, "ctas_per_sm": e.ctas_per_sm, "ms": e.ms}
+
+
+def tune_cache_put(path: str, key: str, paired: int, tile_q: int, ctas_per_sm: int, ms: float = 0.0) -> None:
+    """Write one entry of an autotune cache file (host only)."""
+    e = TuneEntry(int(paired), int(tile_q), int(ctas_per_sm), 0, float(ms))
+    _check(load_library().nr_tune_cache_put(path.encode(), key.encode(), ctypes.byref(e)))
+
+
+def debug_fail_allocs(count: int) -> None:
+    """Testing hook: the next `count` device allocations of the library fail
+    as out-of-memory (NR_ENOMEM) without calling cudaMalloc."""
+    _check(load_library().nr_debug_fail_allocs(int(count)))
+
+
 def vi_phi_size(P: int) -> int:
     """Entries of one restart's variational parameters: mu [P] and the packed
     lower triangle of L [P (P + 1) / 2]."""
@@ -423,11 +467,30 @@ def loglik_grad_noalloc(batch: Batch, n_quad: int, ll_out, grad_out, flags_out=N
     """Log-likelihood and gradient through nr_loglik_grad_noalloc, for hosts
     that may not allocate device memory: the caller passes device outputs
     (and optionally a device int32 for the error flags); the library
-    allocates nothing."""
+    allocates nothing.  Either output may be None (not computed into).  The
+    C ABI cannot see buffer sizes, so they are checked here: ll_out holds at
+    least n_stacks float64 values, grad_out at least params.numel(), both
+    contiguous on the batch's device."""
+    import torch
+
+    def dev_ptr(t, name, dtype, numel):
+        if t is None:
+            return None
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device == batch.params.device):
+            raise ValueError(f"{name} must be a CUDA tensor on the batch's device")
+        if t.dtype != dtype or not t.is_contiguous() or t.numel() < numel:
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor of at least {numel} elements")
+        return t.data_ptr()
+
+    if batch.on_host:
+        raise ValueError("nr_loglik_grad_noalloc takes device-memory batches only")
+    p_ll = dev_ptr(ll_out, "ll_out", torch.float64, batch.n_stacks)
+    p_g = dev_ptr(grad_out, "grad_out", torch.float64, batch.params.numel())
+    p_f = dev_ptr(flags_out, "flags_out", torch.int32, 1)
     cb = batch._c()
     _check(load_library().nr_loglik_grad_noalloc(
-        ctypes.byref(cb), n_quad, ctypes.c_void_p(ll_out.data_ptr()), ctypes.c_void_p(grad_out.data_ptr()),
-        ctypes.c_void_p(flags_out.data_ptr() if flags_out is not None else None), _stream_handle(stream)))
+        ctypes.byref(cb), n_quad, ctypes.c_void_p(p_ll), ctypes.c_void_p(p_g), ctypes.c_void_p(p_f),
+        _stream_handle(stream)))
 
 
 def _autograd_function():

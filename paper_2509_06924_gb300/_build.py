@@ -20,7 +20,7 @@ PEAK_SOURCE = "nr_peak.cu"
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["nr_mixed.cu", "nr_pair.cu", "nr_fp64.cu", "nr_noalloc.cu", "nr_profile.cu", "nr_hmc.cu", "nr_vi.cu"]
-CPP_SOURCES = ["nr_api.cpp"]
+CPP_SOURCES = ["nr_api.cpp", "nr_tune.cpp"]
 HEADERS = ["nr_internal.h", "nr_device.cuh"]
 
 

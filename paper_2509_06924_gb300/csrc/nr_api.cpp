@@ -3,6 +3,7 @@
 // per-batch device work lists, cached by metadata), launch-shape choice and
 // autotuning, host-memory staging, and the device status word.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -14,6 +15,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "nr.h"
 #include "nr_internal.h"
@@ -64,7 +66,8 @@ double herm_psi(int K, double x, double *dpsi)
 bool gauss_hermite(int K, double *x, double *w)
 {
     if (K < 1 || K > NR_MAX_QUAD) return false;
-    std::vector<double> A((size_t)K * K, 0.0);
+    // fixed-size storage: no heap allocation (nr_loglik_grad_noalloc uses this)
+    double A[NR_MAX_QUAD * NR_MAX_QUAD] = {};
     for (int i = 0; i + 1 < K; ++i) A[i * K + i + 1] = A[(i + 1) * K + i] = std::sqrt((i + 1) / 2.0);
     for (int sweep = 0; sweep < 100; ++sweep) {
         double off = 0.0;
@@ -90,9 +93,9 @@ bool gauss_hermite(int K, double *x, double *w)
                 }
             }
     }
-    std::vector<double> nodes(K);
+    double nodes[NR_MAX_QUAD];
     for (int i = 0; i < K; ++i) nodes[i] = A[i * K + i];
-    std::sort(nodes.begin(), nodes.end());
+    std::sort(nodes, nodes + K);
     for (int i = 0; i < K; ++i) {
         double xi = nodes[i], d;
         for (int it = 0; it < 3; ++it) {
@@ -107,6 +110,20 @@ bool gauss_hermite(int K, double *x, double *w)
 }
 
 // --------------------------------------------------------------- buffers --
+// Allocation-failure injection for tests (nr_debug_fail_allocs): the next
+// g_fail_allocs device allocations of the library report
+// cudaErrorMemoryAllocation without calling cudaMalloc.
+std::atomic<int> g_fail_allocs{0};
+
+cudaError_t dev_malloc(void **p, size_t n)
+{
+    int k = g_fail_allocs.load();
+    while (k > 0 && !g_fail_allocs.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k > 0) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, n);
+}
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
@@ -120,11 +137,18 @@ struct DevBuf {
             p = nullptr;
             bytes = 0;
         }
-        cudaError_t e = cudaMalloc(&p, n);
+        cudaError_t e = dev_malloc(&p, n);
         if (e == cudaSuccess) bytes = n;
+        else p = nullptr;
         return e;
     }
     template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// NVTX range around a library call (no cost without a profiler attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
 };
 
 constexpr int kGradBuckets[] = {1, 2, 4, 8, 12, 16, 20, 32, 64};
@@ -181,16 +205,45 @@ struct Plan {
 namespace nrimpl {
 // Message for nr_last_error() from the other translation units.
 void record_error(const char *msg) { g_last_error = msg; }
+
+bool make_quad_const(int K, QuadConst &qc)
+{
+    double x[NR_MAX_QUAD], w[NR_MAX_QUAD];
+    if (!gauss_hermite(K, x, w)) return false;
+    const double c = 1.0 / (2.0 * std::sqrt(std::log(2.0)));
+    const double isp = 1.0 / std::sqrt(M_PI);
+    qc = QuadConst{};
+    qc.K = K;
+    for (int k = 0; k < K; ++k) {
+        const double g = x[k] * c;
+        qc.gd[k] = g;
+        qc.g_hi[k] = (float)g;
+        qc.g_lo[k] = (float)(g - (double)(float)g);
+        qc.wd[k] = w[k] * isp;
+        qc.w[k] = (float)(w[k] * isp);
+    }
+    for (int i = 0; i < 64; ++i) {
+        const double a = 2.0 * M_PI * i / 64.0;
+        qc.cs_tab[i] = (float)std::cos(a);
+        qc.cs_tab[64 + i] = (float)std::sin(a);
+    }
+    return true;
+}
 } // namespace nrimpl
 
 struct nr_ctx {
     int device = 0;
     int sms = 0;
+    char gpu_name[256] = {};
     nr_options opt{};
     QuadConst qc{};
     int32_t *d_status = nullptr;
     std::vector<std::unique_ptr<Plan>> plans;
     uint64_t clock = 0;
+    // side streams and events of the concurrent register-bucket launches
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev_join;
+    cudaEvent_t ev_fork = nullptr;
     // host-memory staging
     DevBuf s_params, s_q, s_dq, s_robs, s_rerr, s_out, s_ll, s_grad, s_res;
     DevBuf p_off, p_nl, p_z, p_rho, p_iota; // SLD-profile metadata and host-call staging
@@ -207,6 +260,7 @@ struct nr_sampler {
     nr_batch batch{};
     DevBuf d_src, d_val, d_lo, d_hi, d_tie_ptr, d_tie_slot, d_params, d_ll, d_gpk, d_mom, d_u0, d_H0, d_lp0;
     DevBuf d_vu, d_vg, d_vlp, d_vpart; // variational step: u = mu + L e, d log pi / du, log pi, ELBO part
+    DevBuf d_vbias;                    // Adam bias corrections of the current iteration (2 doubles)
 };
 
 namespace {
@@ -256,6 +310,26 @@ int tile_for(const nr_ctx *ctx, int mode, int nmax)
     int tq = mixed_tile_q(mode, nmax, ctx->qc.K);
     if (ctx->opt.tile_q > 0) tq = std::min(tq, ctx->opt.tile_q);
     return std::max(tq, 1);
+}
+
+// Side streams (non-blocking) and events for launching `groups` register
+// buckets concurrently; created while a plan is built, i.e. before any
+// stream capture of the calls that use them.
+nr_status ensure_side_streams(nr_ctx *ctx, size_t groups)
+{
+    if (groups < 2 || ctx->opt.serial) return NR_OK;
+    if (!ctx->ev_fork) NR_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    while (ctx->side.size() + 1 < groups) {
+        cudaStream_t s = nullptr;
+        NR_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        ctx->side.push_back(s);
+    }
+    while (ctx->ev_join.size() + 1 < groups) {
+        cudaEvent_t e = nullptr;
+        NR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->ev_join.push_back(e);
+    }
+    return NR_OK;
 }
 
 // Build the work list of one mode family: stacks grouped by register bucket,
@@ -360,7 +434,7 @@ nr_status build_worklist(nr_ctx *ctx, Plan &pl, int mode, WorkList &wl)
         NR_CUDA(cudaMemcpy(wl.d_items.p, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice));
     NR_CUDA(cudaMemset(wl.d_done.p, 0, sizeof(int32_t) * std::max(S, 1)));
     NR_CUDA(cudaMemset(wl.d_ticket.p, 0, sizeof(int32_t) * 2 * std::max<size_t>(wl.groups.size(), 1)));
-    return NR_OK;
+    return ensure_side_streams(ctx, wl.groups.size());
 }
 
 nr_status build_fp64(nr_ctx *ctx, Plan &pl)
@@ -492,15 +566,31 @@ nr_status launch_device(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, floa
     a.stacks = wl.d_stacks.as<StackInfo>();
     a.partials = wl.d_partials.as<double>();
     a.stack_done = wl.d_done.as<int32_t>();
-    for (size_t g = 0; g < wl.groups.size(); ++g) {
+    // Several register buckets: each is its own persistent launch; they run
+    // concurrently on forked streams (joined back into `st` before the call
+    // returns), so the tail of one bucket's queue overlaps the others' work
+    // instead of idling SMs.  Every bucket writes disjoint outputs, partial
+    // slots and tickets.  A fork / join of events is legal in stream capture.
+    const size_t G_n = wl.groups.size();
+    const bool fork = G_n > 1 && !ctx->opt.serial && ctx->side.size() + 1 >= G_n && ctx->ev_join.size() + 1 >= G_n;
+    if (fork) NR_CUDA(cudaEventRecord(ctx->ev_fork, st));
+    for (size_t g = 0; g < G_n; ++g) {
         const Group &G = wl.groups[g];
         a.items = wl.d_items.as<WorkItem>() + G.item_begin;
         a.n_items = G.item_count;
         a.tile_q = G.tile_q;
         a.ticket = wl.d_ticket.as<int32_t>() + 2 * g;
-        cudaError_t e = launch_mixed(mode, G.nmax, G.grid, a, ctx->qc, st, G.pair);
+        cudaStream_t sg = st;
+        if (fork && g > 0) {
+            sg = ctx->side[g - 1];
+            NR_CUDA(cudaStreamWaitEvent(sg, ctx->ev_fork, 0));
+        }
+        cudaError_t e = launch_mixed(mode, G.nmax, G.grid, a, ctx->qc, sg, G.pair);
         if (e != cudaSuccess) return fail(NR_ECUDA, "mixed launch (bucket %d): %s", G.nmax, cudaGetErrorString(e));
+        if (fork && g > 0) NR_CUDA(cudaEventRecord(ctx->ev_join[g - 1], sg));
     }
+    if (fork)
+        for (size_t g = 1; g < G_n; ++g) NR_CUDA(cudaStreamWaitEvent(st, ctx->ev_join[g - 1], 0));
     return NR_OK;
 }
 
@@ -508,9 +598,24 @@ nr_status launch_device(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, floa
 // batches, NR_MIXED): for every register bucket of a work list, time the
 // candidate launch shapes on the batch's own data and keep the fastest.  The
 // candidates are the paired and the one-evaluation kernel (where both apply)
-// at the widest tile and at half of it, each at the grid its occupancy
-// allows.  The work items (chunking) stay as planned.  Outputs go to scratch
-// buffers; the device status word sees the timing launches like any call.
+// x the widest tile and half of it x the occupancy limit of CTAs per SM, one
+// fewer and half of it (each a grid of that many CTAs per SM).  The work
+// items (chunking) stay as planned.  Outputs go to scratch buffers; the
+// device status word sees the timing launches like any call.  With
+// NR_TUNE_CACHE set, a bucket whose key is in the cache file takes the
+// stored shape without timing, and new choices are appended to the file.
+constexpr int kTunerVersion = 2;
+
+std::string tune_key(const nr_ctx *ctx, int mode, int nmax, int items)
+{
+    int lg = 0;
+    while ((1 << (lg + 1)) <= items) ++lg;
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|%d|%d|%d|%d|%d|t%d", ctx->gpu_name, ctx->sms, is_grad_mode(mode) ? 2 : 0,
+             ctx->qc.K, nmax, lg, kTunerVersion);
+    return buf;
+}
+
 nr_status autotune_worklist(nr_ctx *ctx, Plan &pl, const nr_batch *b, bool grad)
 {
     WorkList &wl = grad ? pl.grad : pl.fwd;
@@ -519,6 +624,8 @@ nr_status autotune_worklist(nr_ctx *ctx, Plan &pl, const nr_batch *b, bool grad)
     const int mode = grad ? kGrad : (lik ? kLoglik : kModel);
     if (mode != kModel && !lik) return NR_OK;
     const int K = ctx->qc.K;
+    const char *cache = std::getenv("NR_TUNE_CACHE");
+    if (cache && !*cache) cache = nullptr;
     DevBuf out, ll, gr;
     if (mode == kModel) NR_CUDA(out.ensure(sizeof(float) * std::max<int64_t>(pl.total_out, 1)));
     else NR_CUDA(ll.ensure(sizeof(double) * pl.S));
@@ -547,40 +654,74 @@ nr_status autotune_worklist(nr_ctx *ctx, Plan &pl, const nr_batch *b, bool grad)
         a.items = wl.d_items.as<WorkItem>() + G.item_begin;
         a.n_items = G.item_count;
         a.ticket = wl.d_ticket.as<int32_t>() + 2 * g;
+        const std::string key = tune_key(ctx, mode, G.nmax, G.item_count);
+        nr_tune_entry hit{};
+        if (cache && nr_tune_cache_get(cache, key.c_str(), &hit) == NR_OK && hit.tile_q >= 1 &&
+            hit.ctas_per_sm >= 1) {
+            const bool pv = hit.paired && pair_eligible(mode, G.nmax, K);
+            int tmax = mixed_tile_q(mode, G.nmax, K, pv);
+            if (ctx->opt.tile_q > 0) tmax = std::min(tmax, ctx->opt.tile_q);
+            int occ = 1;
+            ce = mixed_occupancy(mode, G.nmax, K, &occ, pv);
+            if (ce != cudaSuccess) break;
+            G.pair = pv;
+            G.tile_q = std::max(1, std::min(hit.tile_q, tmax));
+            G.grid = std::max(1, (int)std::min<int64_t>(G.item_count,
+                                                        (int64_t)ctx->sms * std::min(hit.ctas_per_sm, std::max(occ, 1))));
+            continue;
+        }
         float best_ms = 0.f;
         Group best = G;
+        int best_ctas = 0;
         for (int pv = 1; pv >= 0 && ce == cudaSuccess; --pv) {
             if (pv == 1 && !pair_eligible(mode, G.nmax, K)) continue;
             int occ = 1;
             ce = mixed_occupancy(mode, G.nmax, K, &occ, pv == 1);
             if (ce != cudaSuccess) break;
-            int grid = (int)std::min<int64_t>(G.item_count, (int64_t)ctx->sms * std::max(occ, 1));
-            if (ctx->opt.grid_ctas > 0) grid = std::min(G.item_count, ctx->opt.grid_ctas);
-            grid = std::max(grid, 1);
+            occ = std::max(occ, 1);
             int tmax = mixed_tile_q(mode, G.nmax, K, pv == 1);
             if (ctx->opt.tile_q > 0) tmax = std::min(tmax, ctx->opt.tile_q);
             tmax = std::max(tmax, 1);
-            for (int tq : {tmax, tmax / 2}) {
-                if (tq < 1) continue;
-                a.tile_q = tq;
-                ce = launch_mixed(mode, G.nmax, grid, a, ctx->qc, st, pv == 1); // warm-up
-                if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
-                for (int r = 0; r < kReps && ce == cudaSuccess; ++r)
-                    ce = launch_mixed(mode, G.nmax, grid, a, ctx->qc, st, pv == 1);
-                if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
-                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-                float ms = 0.f;
-                if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
-                if (ce != cudaSuccess) break;
-                if (best_ms == 0.f || ms < best_ms) {
-                    best_ms = ms;
-                    best.pair = pv == 1;
-                    best.tile_q = tq;
-                    best.grid = grid;
+            int cands[3] = {occ, occ - 1, (occ + 1) / 2};
+            for (int ci = 0; ci < 3 && ce == cudaSuccess; ++ci) {
+                const int cps = cands[ci];
+                if (cps < 1 || (ci > 0 && cps == cands[0]) || (ci == 2 && cps == cands[1])) continue;
+                int grid = (int)std::min<int64_t>(G.item_count, (int64_t)ctx->sms * cps);
+                if (ctx->opt.grid_ctas > 0) grid = std::min(G.item_count, ctx->opt.grid_ctas);
+                grid = std::max(grid, 1);
+                for (int tq : {tmax, tmax / 2}) {
+                    if (tq < 1) continue;
+                    a.tile_q = tq;
+                    ce = launch_mixed(mode, G.nmax, grid, a, ctx->qc, st, pv == 1); // warm-up
+                    if (ce == cudaSuccess) ce = cudaEventRecord(e0, st);
+                    for (int r = 0; r < kReps && ce == cudaSuccess; ++r)
+                        ce = launch_mixed(mode, G.nmax, grid, a, ctx->qc, st, pv == 1);
+                    if (ce == cudaSuccess) ce = cudaEventRecord(e1, st);
+                    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                    if (ce != cudaSuccess) break;
+                    if (best_ms == 0.f || ms < best_ms) {
+                        best_ms = ms;
+                        best.pair = pv == 1;
+                        best.tile_q = tq;
+                        best.grid = grid;
+                        best_ctas = cps;
+                    }
                 }
             }
         }
-        if (ce == cudaSuccess) G = best;
+        if (ce == cudaSuccess) {
+            G = best;
+            if (cache) {
+                nr_tune_entry e{};
+                e.paired = best.pair ? 1 : 0;
+                e.tile_q = best.tile_q;
+                e.ctas_per_sm = best_ctas;
+                e.ms = best_ms / kReps;
+                nr_tune_cache_put(cache, key.c_str(), &e); // best effort: a read-only cache still tunes
+            }
+        }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -640,6 +781,8 @@ nr_status run_host(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, float *r_
 nr_status compute(nr_ctx *ctx, const nr_batch *b, int mode, float *r_out, double *ll, double *grad, double *gres,
                   void *stream)
 {
+    static const char *const kNames[] = {"nr_reflectivity", "nr_loglik", "nr_loglik_grad", "nr_loglik_grad_res"};
+    NvtxRange range(kNames[mode]);
     if (!ctx) return fail(NR_EINVAL, "context is NULL");
     if (!b) return fail(NR_EINVAL, "batch is NULL");
     if (mode == kModel && !r_out && b->n_stacks > 0) return fail(NR_EINVAL, "r_out is NULL");
@@ -680,23 +823,17 @@ nr_status nr_create(nr_ctx **out, const nr_options *opt)
         return fail(NR_EINVAL, "unknown precision %d", ctx->opt.precision);
     if (ctx->opt.tile_q < 0 || ctx->opt.chunk_q < 0 || ctx->opt.grid_ctas < 0)
         return fail(NR_EINVAL, "negative launch override");
-    double x[NR_MAX_QUAD], w[NR_MAX_QUAD];
-    const int K = ctx->opt.n_quad;
-    if (!gauss_hermite(K, x, w)) return fail(NR_EINVAL, "quadrature failed");
-    const double c = 1.0 / (2.0 * std::sqrt(std::log(2.0)));
-    const double isp = 1.0 / std::sqrt(M_PI);
-    ctx->qc.K = K;
-    for (int k = 0; k < K; ++k) {
-        const double g = x[k] * c;
-        ctx->qc.gd[k] = g;
-        ctx->qc.g_hi[k] = (float)g;
-        ctx->qc.g_lo[k] = (float)(g - (double)(float)g);
-        ctx->qc.wd[k] = w[k] * isp;
-        ctx->qc.w[k] = (float)(w[k] * isp);
-    }
+    if (!make_quad_const(ctx->opt.n_quad, ctx->qc)) return fail(NR_EINVAL, "quadrature failed");
     NR_CUDA(cudaGetDevice(&ctx->device));
     NR_CUDA(cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    NR_CUDA(cudaMalloc(&ctx->d_status, sizeof(int32_t)));
+    {
+        cudaDeviceProp prop{};
+        NR_CUDA(cudaGetDeviceProperties(&prop, ctx->device));
+        snprintf(ctx->gpu_name, sizeof ctx->gpu_name, "%s", prop.name);
+        for (char *c = ctx->gpu_name; *c; ++c)
+            if (*c == '"' || *c == '\\' || *c == '|') *c = '_';
+    }
+    NR_CUDA(dev_malloc(reinterpret_cast<void **>(&ctx->d_status), sizeof(int32_t)));
     NR_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int32_t)));
     *out = ctx.release();
     return NR_OK;
@@ -708,6 +845,9 @@ void nr_destroy(nr_ctx *ctx)
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     if (ctx->d_status) cudaFree(ctx->d_status);
+    for (cudaStream_t s : ctx->side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : ctx->ev_join) cudaEventDestroy(e);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     delete ctx;
 }
 
@@ -871,6 +1011,7 @@ nr_status nr_sampler_create(nr_ctx *ctx, const nr_cofit_model *m, nr_sampler **o
     NR_CUDA(S.d_vg.ensure(sizeof(double) * (size_t)C * P));
     NR_CUDA(S.d_vlp.ensure(sizeof(double) * C));
     NR_CUDA(S.d_vpart.ensure(sizeof(double) * C));
+    NR_CUDA(S.d_vbias.ensure(sizeof(double) * 2));
     NR_CUDA(cudaMemcpy(S.d_src.p, m->slot_src, sizeof(int32_t) * NS, cudaMemcpyHostToDevice));
     NR_CUDA(cudaMemcpy(S.d_val.p, m->slot_val, sizeof(double) * NS, cudaMemcpyHostToDevice));
     NR_CUDA(cudaMemcpy(S.d_lo.p, m->lo, sizeof(double) * P, cudaMemcpyHostToDevice));
@@ -991,7 +1132,8 @@ nr_status nr_vi_step(nr_sampler *S, double *phi, double *adam_m, double *adam_v,
     NR_CUDA(cudaSetDevice(S->ctx->device));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     double *u = S->d_vu.as<double>();
-    cudaError_t e = launch_vi_sample(phi, eps, S->C, S->P, u, S->d_vpart.as<double>(), t, st);
+    cudaError_t e = launch_vi_sample(phi, eps, S->C, S->P, u, S->d_vpart.as<double>(), t, opt->beta1, opt->beta2,
+                                     S->d_vbias.as<double>(), st);
     if (e != cudaSuccess) return fail(NR_ECUDA, "vi sample: %s", cudaGetErrorString(e));
     nr_status r = sampler_eval(S, u, st);
     if (r != NR_OK) return r;
@@ -1001,7 +1143,8 @@ nr_status nr_vi_step(nr_sampler *S, double *phi, double *adam_m, double *adam_v,
     e = launch_cofit_stage(a, st);
     if (e == cudaSuccess)
         e = launch_vi_adam(phi, adam_m, adam_v, eps, S->d_vg.as<double>(), S->d_vlp.as<double>(),
-                           S->d_vpart.as<double>(), S->C, S->P, t, opt->lr, opt->beta1, opt->beta2, opt->eps, elbo,
+                           S->d_vpart.as<double>(), S->C, S->P, S->d_vbias.as<double>(), opt->lr, opt->beta1,
+                           opt->beta2, opt->eps, elbo,
                            st);
     if (e != cudaSuccess) return fail(NR_ECUDA, "vi step: %s", cudaGetErrorString(e));
     return NR_OK;
@@ -1041,6 +1184,36 @@ nr_status nr_plan_info(nr_ctx *ctx, const nr_batch *batch, int64_t *evals, int32
     if (chunk_q) *chunk_q = fp64 ? kFp64Block : wl.chunk_q;
     if (grid_ctas) *grid_ctas = fp64 ? pl->n64_items : (wl.groups.empty() ? 0 : wl.groups[0].grid);
     if (launches) *launches = fp64 ? 2 : (int32_t)wl.groups.size();
+    return NR_OK;
+}
+
+nr_status nr_debug_fail_allocs(int32_t count)
+{
+    if (count < 0) return fail(NR_EINVAL, "count < 0");
+    g_fail_allocs.store(count);
+    return NR_OK;
+}
+
+nr_status nr_plan_groups(nr_ctx *ctx, const nr_batch *batch, int32_t grad, int32_t max_groups, int32_t *count,
+                         int32_t *nmax, int32_t *paired, int32_t *tile_q, int32_t *grid, int32_t *items)
+{
+    if (!ctx) return fail(NR_EINVAL, "context is NULL");
+    if (max_groups < 0) return fail(NR_EINVAL, "max_groups < 0");
+    if (ctx->opt.precision != NR_MIXED) return fail(NR_EINVAL, "launch groups exist for NR_MIXED contexts only");
+    NR_CUDA(cudaSetDevice(ctx->device));
+    Plan *pl = nullptr;
+    nr_status st = get_plan(ctx, batch, grad ? kGrad : kModel, &pl);
+    if (st != NR_OK) return st;
+    const WorkList &wl = grad ? pl->grad : pl->fwd;
+    if (count) *count = (int32_t)wl.groups.size();
+    for (int i = 0; i < (int)wl.groups.size() && i < max_groups; ++i) {
+        const Group &G = wl.groups[i];
+        if (nmax) nmax[i] = G.nmax;
+        if (paired) paired[i] = G.pair && pair_eligible(grad ? kGrad : kLoglik, G.nmax, ctx->qc.K) ? 1 : 0;
+        if (tile_q) tile_q[i] = G.tile_q;
+        if (grid) grid[i] = G.grid;
+        if (items) items[i] = G.item_count;
+    }
     return NR_OK;
 }
 

@@ -72,6 +72,49 @@ __device__ __forceinline__ void sincos_approx(float x, float &sn, float &cs)
     asm("sin.approx.ftz.f32 %0, %1;" : "=f"(sn) : "f"(x));
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cs) : "f"(x));
 }
+// sin / cos of the layer phases and of the Nevot-Croce factors.
+// NR_SINCOS_TABLE 1: a 64-entry table of cos / sin at multiples of 2 pi / 64
+// (correctly rounded on the host, staged in shared memory) and a short
+// Taylor polynomial for the remainder |x| <= pi / 64 (truncation below 3e-9),
+// combined by the angle-addition formula: about 1e-7 absolute, on the FMA
+// pipe plus one shared load.  0: the special-function unit's sin.approx /
+// cos.approx (about 5e-7 absolute over [-pi, pi]).  Near a waveguide
+// resonance the gradient amplifies the phase error by 10^2 - 10^3, which
+// the table keeps within the tolerance where the special-function unit did
+// not.
+#ifndef NR_SINCOS_TABLE
+#define NR_SINCOS_TABLE 0
+#endif
+// the same choice for the Nevot-Croce factors (defaults to the phases')
+#ifndef NR_NC_TABLE
+#define NR_NC_TABLE NR_SINCOS_TABLE
+#endif
+
+constexpr int kTabN = 64;
+constexpr float kTabScale = 10.18591594696045f;      // 64 / (2 pi)
+constexpr float kTabStepHi = 0.09817477315664291f;   // float(2 pi / 64)
+constexpr float kTabStepLo = -2.7319617679211206e-09f; // 2 pi / 64 - kTabStepHi
+
+// (cos, sin) of ph + pl (pl a low-order correction, |pl| << 1): reduction
+// by multiples of 2 pi / 64 (the multiple rounded with the 1.5 * 2^23
+// addition, whose low mantissa bits are then the table index), remainder
+// polynomial sin x ~ x - x^3 / 6, cos x ~ 1 - x^2 / 2 + x^4 / 24.  tab:
+// cos at [i], sin at [kTabN + i].
+__device__ __forceinline__ float2 cis_tab(float ph, float pl, const float *tab)
+{
+    const float t = fmaf(ph, kTabScale, kRoundMagic);
+    const float nt = __fadd_rn(t, -kRoundMagic);
+    const int i = __float_as_int(t) & (kTabN - 1);
+    const float2 cs = make_float2(tab[i], tab[kTabN + i]);
+    float x = fmaf(-nt, kTabStepHi, ph);
+    x = fmaf(-nt, kTabStepLo, x);
+    x = __fadd_rn(x, pl);
+    const float z = x * x;
+    const float sn = fmaf(x * z, -1.f / 6.f, x);
+    const float cn = fmaf(z, fmaf(z, 1.f / 24.f, -0.5f), 1.f);
+    return make_float2(fmaf(cs.x, cn, -cs.y * sn), fmaf(cs.y, cn, cs.x * sn));
+}
+
 __device__ __forceinline__ float rsqrt_approx(float x)
 {
     float r;
@@ -192,7 +235,7 @@ __device__ __forceinline__ Kz medium_kz(float p_hi, float p_lo, float4 m)
 // reduced modulo 2 pi (Cody-Waite, two-word 2 pi; the multiple of 2 pi is
 // rounded with the 1.5 * 2^23 addition) before the FP32 sincos.
 // L = (2 d as (hi, lo), ea = -2 d log2(e), -): |E| = 2^(Im(k) ea).
-__device__ __forceinline__ float2 layer_phase(const Kz &k, float4 L)
+__device__ __forceinline__ float2 layer_phase(const Kz &k, float4 L, const float *tab)
 {
     const float2 d2 = make_float2(L.x, L.y);
     const float ea = L.z;
@@ -201,14 +244,19 @@ __device__ __forceinline__ float2 layer_phase(const Kz &k, float4 L)
     float pl = fmaf(t, d2.x, -ph);
     pl = fmaf(t, d2.y, pl);
     pl = fmaf(tl, d2.x, pl);
+    const float amp = ex2_approx(k.im * ea);
+#if NR_SINCOS_TABLE
+    const float2 e = cis_tab(ph, pl, tab);
+    return make_float2(amp * e.x, amp * e.y);
+#else
     const float nt = __fadd_rn(fmaf(ph, kInv2Pi, kRoundMagic), -kRoundMagic);
     float red = fmaf(-nt, kTwoPiHi, ph);
     red = fmaf(-nt, kTwoPiLo, red);
     red += pl;
     float s, c;
     sincos_approx(red, s, c);
-    const float amp = ex2_approx(k.im * ea);
     return make_float2(amp * c, amp * s);
+#endif
 }
 
 // r_j with Nevot-Croce roughness; also returns G = exp(s k_a k_b) / S^2 with
@@ -216,7 +264,7 @@ __device__ __forceinline__ float2 layer_phase(const Kz &k, float4 L)
 // sl = s log2(e)).  REAL_A:
 // k_a is real (the fronting medium), its imaginary part is not read.
 template <bool REAL_A>
-__device__ __forceinline__ float2 fresnel_nc(float2 ka, float2 kb, float4 I, float2 &G, float2 &kk)
+__device__ __forceinline__ float2 fresnel_nc(float2 ka, float2 kb, float4 I, float2 &G, float2 &kk, const float *tab)
 {
     const float2 N = make_float2(I.x, I.y);
     const float s = I.z, sl = I.w;
@@ -230,9 +278,14 @@ __device__ __forceinline__ float2 fresnel_nc(float2 ka, float2 kb, float4 I, flo
     float2 F = make_float2(amp, 0.f);
     const float wi = s * kk.y;
     if (NR_BRANCHFREE || wi != 0.f) {
+#if NR_NC_TABLE
+        const float2 e = cis_tab(wi, 0.f, tab);
+        F = make_float2(amp * e.x, amp * e.y);
+#else
         float sn, cs;
         sincos_approx(wi, sn, cs);
         F = make_float2(amp * cs, amp * sn);
+#endif
     }
     G = cmul(F, iS2);
     return cmul(N, G);

@@ -48,8 +48,15 @@ struct QuadConst {
     float w[NR_MAX_QUAD];
     double gd[NR_MAX_QUAD];
     double wd[NR_MAX_QUAD];
+    // cos(2 pi i / 64) at [i], sin at [64 + i], i < 64, correctly rounded:
+    // the table of the kernels' sin / cos (nr_device.cuh, cis_tab)
+    float cs_tab[128];
     int32_t K;
 };
+
+// The library's K-point Gauss-Hermite rule in the kernels' form (nr_api.cpp;
+// host).  Returns false for K outside [1, NR_MAX_QUAD].
+bool make_quad_const(int K, QuadConst &qc);
 
 struct KernelArgs {
     const double *params;
@@ -135,10 +142,12 @@ cudaError_t launch_cofit_gather(const double *u, int C, int P, int NS, const int
                                 const double *lo, const double *hi, double *params, cudaStream_t st);
 cudaError_t launch_cofit_stage(const CofitStageArgs &a, cudaStream_t st);
 // variational inference (nr_vi.cu)
+// vi_sample advances the device iteration counter and writes the Adam bias
+// corrections 1 / (1 - beta1^t), 1 / (1 - beta2^t) to bias[0..1]
 cudaError_t launch_vi_sample(const double *phi, const double *eps, int R, int P, double *u, double *part,
-                             int32_t *t_dev, cudaStream_t st);
+                             int32_t *t_dev, double beta1, double beta2, double *bias, cudaStream_t st);
 cudaError_t launch_vi_adam(double *phi, double *m, double *v, const double *eps, const double *g,
-                           const double *logp, const double *part, int R, int P, const int32_t *t_dev, double lr,
+                           const double *logp, const double *part, int R, int P, const double *bias, double lr,
                            double beta1, double beta2, double eps_adam, double *elbo, cudaStream_t st);
 
 // Raw per-stack sums of the mixed gradient kernels, and the stride of a

@@ -126,6 +126,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     constexpr int EQ = T::EQ_CAP;
 
     __shared__ StackSmem<NM> sm;
+    __shared__ float sh_cs[2 * kTabN];                   // cos, sin at multiples of 2 pi / 64
     __shared__ __align__(16) float sh_wR[2][2 * BLOCK]; // w_k R per (Q slot, node), double-buffered
     // the super-tile's data per Q point: (Q/2, dQ/2, R_obs, 1/err), and the
     // (residual, smeared R) pairs its tiles leave for the likelihood sums
@@ -170,6 +171,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     const float g_max = fmaxf(fabsf(qc.g_hi[0]), fabsf(qc.g_hi[K - 1]));
 
     for (int i = tid; i < 4 * BLOCK; i += BLOCK) (&sh_wR[0][0])[i] = 0.f; // padding stays 0
+    for (int i = tid; i < 2 * kTabN; i += BLOCK) sh_cs[i] = qc.cs_tab[i];   // read after the item barrier
 
     for (;;) {
         if (tid == 0) sh_item = atomicAdd(&ka.ticket[0], 1);
@@ -383,14 +385,14 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 float2 Gj, kkj;
                 // k_0 is real: the real-k_a form there
                 const float4 Ij = sm.itf[j];
-                const float2 rj = top ? fresnel_nc<true>(kc(kj), kc(kbelow), Ij, Gj, kkj)
-                                      : fresnel_nc<false>(kc(kj), kc(kbelow), Ij, Gj, kkj);
+                const float2 rj = top ? fresnel_nc<true>(kc(kj), kc(kbelow), Ij, Gj, kkj, sh_cs)
+                                      : fresnel_nc<false>(kc(kj), kc(kbelow), Ij, Gj, kkj, sh_cs);
                 float2 Xj;
                 if (bot) {
                     Xj = rj;
                     if constexpr (T::STORE) kst[j + 1] = kbelow;
                 } else {
-                    const float2 Ej = layer_phase(kbelow, sm.lay[j + 1]);
+                    const float2 Ej = layer_phase(kbelow, sm.lay[j + 1], sh_cs);
                     const float2 Yj = cmul(Xbelow, Ej);
                     float2 Dj;
                     Xj = mobius(rj, Yj, Dj);
@@ -496,8 +498,8 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                     } else {
                         const float4 Mj1 = sm.med[j + 1];
                         kj1 = bot ? medium_kz<false>(p_hi, p_lo, Mj1) : medium_kz<true>(p_hi, p_lo, Mj1);
-                        rj = top ? fresnel_nc<true>(kc(kj), kc(kj1), Ij, Gj, kkj)
-                                 : fresnel_nc<false>(kc(kj), kc(kj1), Ij, Gj, kkj);
+                        rj = top ? fresnel_nc<true>(kc(kj), kc(kj1), Ij, Gj, kkj, sh_cs)
+                                 : fresnel_nc<false>(kc(kj), kc(kj1), Ij, Gj, kkj, sh_cs);
                     }
                     float2 kbar1 = make_float2(0.f, 0.f);
                     float2 rb;
@@ -509,7 +511,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                             Dj = Dst[j];
                             Y = Yst[j];
                         } else {
-                            Ej1 = layer_phase(kj1, Lj1);
+                            Ej1 = layer_phase(kj1, Lj1, sh_cs);
                             Y = cmul(X1, Ej1);
                             const float2 rY = cmul(rj, Y);
                             const float dx = 1.f + rY.x, dy = rY.y;

@@ -11,12 +11,17 @@
 // of fixed size that every GPU loading the library holds until the process
 // exits, and the caller passes only inputs and outputs.
 //
-// The computation is the regular mixed-precision gradient kernel, launched
-// once per layer bucket with one work item per stack (no chunking).
+// The computation is the regular mixed-precision gradient kernel (the paired
+// two-evaluations-per-thread kernel wherever nr_loglik_grad uses it),
+// launched once per layer bucket with one work item per stack (no chunking).
+// The work list is built on the host in static arrays and copied from that
+// pageable memory, so the call waits for the stream's earlier work before it
+// returns; the kernels then run asynchronously.  It cannot be captured in a
+// CUDA graph (refused with NR_EINVAL): a replay would copy whatever the last
+// eager call left in the host arrays.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
@@ -53,69 +58,6 @@ nr_status err(nr_status st, const char *what)
 {
     record_error(what);
     return st;
-}
-
-// Gauss-Hermite nodes with fixed-size storage (K <= NR_MAX_QUAD): Jacobi
-// eigenvalues of the Hermite recurrence matrix, Newton-polished, weights
-// 2 / psi_K'(x)^2.
-double psi(int K, double x, double *d)
-{
-    double pm1 = 0.0, p = 1.0 / std::sqrt(std::sqrt(M_PI));
-    for (int j = 0; j < K; ++j) {
-        const double pn = x * std::sqrt(2.0 / (j + 1)) * p - std::sqrt((double)j / (j + 1)) * pm1;
-        pm1 = p;
-        p = pn;
-    }
-    *d = std::sqrt(2.0 * K) * pm1;
-    return p;
-}
-
-void quadrature(int K, QuadConst &qc)
-{
-    double A[NR_MAX_QUAD][NR_MAX_QUAD] = {};
-    for (int i = 0; i + 1 < K; ++i) A[i][i + 1] = A[i + 1][i] = std::sqrt((i + 1) / 2.0);
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0;
-        for (int p = 0; p < K; ++p)
-            for (int q = p + 1; q < K; ++q) off += A[p][q] * A[p][q];
-        if (off < 1e-30) break;
-        for (int p = 0; p < K; ++p)
-            for (int q = p + 1; q < K; ++q) {
-                if (std::fabs(A[p][q]) < 1e-300) continue;
-                const double th = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
-                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
-                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < K; ++k) {
-                    const double akp = A[k][p], akq = A[k][q];
-                    A[k][p] = c * akp - s * akq;
-                    A[k][q] = s * akp + c * akq;
-                }
-                for (int k = 0; k < K; ++k) {
-                    const double apk = A[p][k], aqk = A[q][k];
-                    A[p][k] = c * apk - s * aqk;
-                    A[q][k] = s * apk + c * aqk;
-                }
-            }
-    }
-    double x[NR_MAX_QUAD];
-    for (int i = 0; i < K; ++i) x[i] = A[i][i];
-    std::sort(x, x + K);
-    const double cg = 1.0 / (2.0 * std::sqrt(std::log(2.0))), isp = 1.0 / std::sqrt(M_PI);
-    qc.K = K;
-    for (int i = 0; i < K; ++i) {
-        double xi = x[i], d;
-        for (int it = 0; it < 3; ++it) {
-            const double f = psi(K, xi, &d);
-            if (d != 0.0) xi -= f / d;
-        }
-        psi(K, xi, &d);
-        const double g = xi * cg, w = 2.0 / (d * d) * isp;
-        qc.gd[i] = g;
-        qc.g_hi[i] = (float)g;
-        qc.g_lo[i] = (float)(g - (double)(float)g);
-        qc.wd[i] = w;
-        qc.w[i] = (float)w;
-    }
 }
 
 int bucket_of(int n)
@@ -155,6 +97,17 @@ extern "C" nr_status nr_loglik_grad_noalloc(const nr_batch *b, int32_t n_quad, d
         if (b->dataset[s] < 0 || b->dataset[s] >= b->n_datasets) return err(NR_EINVAL, "dataset out of range");
     }
 
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // The work list is staged in static host arrays that the next call
+    // overwrites: a captured copy would replay whatever the latest eager call
+    // left there, against the grids fixed at capture time.  So a capturing
+    // stream is refused before anything is enqueued.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return err(NR_ECUDA, "cudaStreamIsCapturing failed");
+    if (cap != cudaStreamCaptureStatusNone)
+        return err(NR_EINVAL, "nr_loglik_grad_noalloc cannot be captured in a CUDA graph (its work list is "
+                              "staged in host memory that every call rewrites)");
+
     std::lock_guard<std::mutex> lock(g_mutex);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return err(NR_ECUDA, "cudaGetDevice failed");
@@ -170,7 +123,6 @@ extern "C" nr_status nr_loglik_grad_noalloc(const nr_batch *b, int32_t n_quad, d
     int32_t *d_status = d_tickets + 2 * kNumBuckets;
     StackInfo *d_stacks = reinterpret_cast<StackInfo *>(base + kCtrlBytes);
     WorkItem *d_items = reinterpret_cast<WorkItem *>(base + kCtrlBytes + (size_t)kMaxStacks * sizeof(StackInfo));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     // one work item per stack; items grouped by bucket, longest first
     int64_t par = 0, out = 0;
@@ -216,7 +168,7 @@ extern "C" nr_status nr_loglik_grad_noalloc(const nr_batch *b, int32_t n_quad, d
         return err(NR_ECUDA, "cudaMemcpyAsync of the work list failed");
 
     QuadConst qc{};
-    quadrature(n_quad, qc);
+    if (!make_quad_const(n_quad, qc)) return err(NR_EINVAL, "quadrature failed");
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return err(NR_ECUDA, "cudaDeviceGetAttribute failed");

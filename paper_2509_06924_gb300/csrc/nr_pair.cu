@@ -105,6 +105,22 @@ __device__ __forceinline__ void psincos(f2 a, f2 &s, f2 &c)
     sincos_approx(a.y, s.y, c.y);
 }
 __device__ __forceinline__ float half(f2 a, int h) { return h ? a.y : a.x; }
+// cis_tab (nr_device.cuh) on both halves: (cos, sin) as a complex pair
+__device__ __forceinline__ void pcis_tab(f2 ph, f2 pl, const float *tab, f2 &cs, f2 &sn)
+{
+    const f2 t = pfma(ph, bc(kTabScale), bc(kRoundMagic));
+    const f2 nt = padd(t, bc(-kRoundMagic));
+    const int i0 = __float_as_int(t.x) & (kTabN - 1), i1 = __float_as_int(t.y) & (kTabN - 1);
+    const f2 tc = make_float2(tab[i0], tab[i1]), ts = make_float2(tab[kTabN + i0], tab[kTabN + i1]);
+    f2 x = pfma(pneg(nt), bc(kTabStepHi), ph);
+    x = pfma(pneg(nt), bc(kTabStepLo), x);
+    x = padd(x, pl);
+    const f2 z = pmul(x, x);
+    const f2 sx = pfma(pmul(x, z), bc(-1.f / 6.f), x);
+    const f2 cx = pfma(z, pfma(z, bc(1.f / 24.f), bc(-0.5f)), bc(1.f));
+    cs = pfma(tc, cx, pneg(pmul(ts, sx)));
+    sn = pfma(ts, cx, pmul(tc, sx));
+}
 
 // error-free transformations on both halves (every paired add rounds once)
 __device__ __forceinline__ void two_sum2(f2 a, f2 b, f2 &s, f2 &e)
@@ -199,27 +215,31 @@ __device__ __forceinline__ Kz2 medium_kz2(f2 p_hi, f2 p_lo, float4 m)
     }
 }
 
-// E = exp(2 i k d), phase in double-float reduced mod 2 pi (as layer_phase)
-__device__ __forceinline__ c2 layer_phase2(const Kz2 &k, float4 L)
+// E = exp(2 i k d), phase in double-float (as layer_phase)
+__device__ __forceinline__ c2 layer_phase2(const Kz2 &k, float4 L, const float *tab)
 {
     const f2 ph = pmul(k.re, bc(L.x));
     f2 pl = pfma(k.re, bc(L.x), pneg(ph));
     pl = pfma(k.re, bc(L.y), pl);
     pl = pfma(k.lo, bc(L.x), pl);
+    const f2 amp = pex2(pmul(k.im, bc(L.z)));
+    f2 s, c;
+#if NR_SINCOS_TABLE
+    pcis_tab(ph, pl, tab, c, s);
+#else
     const f2 nt = padd(pfma(ph, bc(kInv2Pi), bc(kRoundMagic)), bc(-kRoundMagic));
     f2 red = pfma(pneg(nt), bc(kTwoPiHi), ph);
     red = pfma(pneg(nt), bc(kTwoPiLo), red);
     red = padd(red, pl);
-    f2 s, c;
     psincos(red, s, c);
-    const f2 amp = pex2(pmul(k.im, bc(L.z)));
+#endif
     return c2{pmul(amp, c), pmul(amp, s)};
 }
 
 // r_j with Nevot-Croce roughness, G = exp(s k_a k_b) / S^2 and kk = k_a k_b
 // (as fresnel_nc).  A vanishing S (k_a = k_b = 0) gives G = r = 0.
 template <bool REAL_A>
-__device__ __forceinline__ c2 fresnel_nc2(c2 ka, c2 kb, float4 I, c2 &G, c2 &kk)
+__device__ __forceinline__ c2 fresnel_nc2(c2 ka, c2 kb, float4 I, c2 &G, c2 &kk, const float *tab)
 {
     const f2 Sx = padd(ka.re, kb.re);
     const f2 Sy = REAL_A ? kb.im : padd(ka.im, kb.im);
@@ -229,7 +249,11 @@ __device__ __forceinline__ c2 fresnel_nc2(c2 ka, c2 kb, float4 I, c2 &G, c2 &kk)
     kk = REAL_A ? c2{pmul(ka.re, kb.re), pmul(ka.re, kb.im)} : cmul2(ka, kb);
     const f2 amp = pex2(pmul(bc(I.w), kk.re));
     f2 sn, cs;
+#if NR_NC_TABLE
+    pcis_tab(pmul(bc(I.z), kk.im), bc(0.f), tab, cs, sn);
+#else
     psincos(pmul(bc(I.z), kk.im), sn, cs);
+#endif
     G = cmul2(c2{pmul(amp, cs), pmul(amp, sn)}, iS2);
     return cmul2(c2{bc(I.x), bc(I.y)}, G);
 }
@@ -326,6 +350,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
     static_assert(CAPQ >= 2 * BLOCK / kSubLanes, "a super-tile holds at least one tile");
 
     __shared__ StackSmem<NM> sm;
+    __shared__ float sh_cs[2 * kTabN]; // cos, sin at multiples of 2 pi / 64
     // w_k R per (Q slot, node), double-buffered.  TQ KP <= 4 BLOCK for any K >= 3;
     // the rolled kernels, short of shared memory, take the exact maximum
     // over K >= 3 (408 at K = 5: 51 Q points x 8)
@@ -386,6 +411,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
     const float g_max = fmaxf(fabsf(qc.g_hi[0]), fabsf(qc.g_hi[K - 1]));
 
     for (int i = tid; i < 2 * WRN; i += BLOCK) (&sh_wR[0][0])[i] = 0.f; // padding stays 0
+    for (int i = tid; i < 2 * kTabN; i += BLOCK) sh_cs[i] = qc.cs_tab[i];  // read after the item barrier
 
     for (;;) {
         if (tid == 0) sh_item = atomicAdd(&ka.ticket[0], 1);
@@ -567,14 +593,14 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                 else kj = medium_kz2<true>(p_hi, p_lo, sm.med[j]);
                 c2 Gj, kkj;
                 const float4 Ij = sm.itf[j];
-                const c2 rj = top ? fresnel_nc2<true>(kc2(kj), kc2(kbelow), Ij, Gj, kkj)
-                                  : fresnel_nc2<false>(kc2(kj), kc2(kbelow), Ij, Gj, kkj);
+                const c2 rj = top ? fresnel_nc2<true>(kc2(kj), kc2(kbelow), Ij, Gj, kkj, sh_cs)
+                                  : fresnel_nc2<false>(kc2(kj), kc2(kbelow), Ij, Gj, kkj, sh_cs);
                 c2 Xj;
                 if (bot) {
                     Xj = rj;
                     if constexpr (!ROLL) kst[j + 1] = kbelow;
                 } else {
-                    const c2 Ej = layer_phase2(kbelow, sm.lay[j + 1]);
+                    const c2 Ej = layer_phase2(kbelow, sm.lay[j + 1], sh_cs);
                     const c2 Yj = cmul2(Xbelow, Ej);
                     c2 Dj;
                     Xj = mobius2(rj, Yj, Dj);
@@ -673,8 +699,8 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                         if constexpr (ROLL) {
                             const float4 Mj1 = sm.med[j + 1];
                             kj1 = bot ? medium_kz2<false>(p_hi, p_lo, Mj1) : medium_kz2<true>(p_hi, p_lo, Mj1);
-                            rj = top ? fresnel_nc2<true>(kc2(kj), kc2(kj1), Ij, Gj, kkj)
-                                     : fresnel_nc2<false>(kc2(kj), kc2(kj1), Ij, Gj, kkj);
+                            rj = top ? fresnel_nc2<true>(kc2(kj), kc2(kj1), Ij, Gj, kkj, sh_cs)
+                                     : fresnel_nc2<false>(kc2(kj), kc2(kj1), Ij, Gj, kkj, sh_cs);
                         } else {
                             kj1 = kst[j + 1];
                             rj = rst[j];
@@ -687,7 +713,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                             c2 Ej1, Dj, Y;
                             if constexpr (ROLL) {
                                 const float4 x1 = sh_X[(j + 1) * BLOCK + tid];
-                                Ej1 = layer_phase2(kj1, Lj1);
+                                Ej1 = layer_phase2(kj1, Lj1, sh_cs);
                                 Y = cmul2(c2{make_float2(x1.x, x1.y), make_float2(x1.z, x1.w)}, Ej1);
                                 const c2 rY = cmul2(rj, Y);
                                 const f2 dx = padd(bc(1.f), rY.re), dy = rY.im;

@@ -30,14 +30,20 @@ constexpr unsigned kMask = 0xffffffffu;
 constexpr double kHalfLog2Pi = 0.91893853320467274178032973640562; // ln(2 pi) / 2
 
 __global__ void vi_sample_kernel(const double *phi, const double *eps, int R, int P, int64_t nphi, double *u,
-                                 double *part, int32_t *t_dev)
+                                 double *part, int32_t *t_dev, double beta1, double beta2, double *bias)
 {
     const int warps = blockDim.x >> 5;
     const int r = blockIdx.x * warps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     // the iteration counter lives on the device, so a captured iteration
-    // advances it on every replay; vi_adam (later in the stream) reads it
-    if (blockIdx.x == 0 && threadIdx.x == 0) *t_dev += 1;
+    // advances it on every replay; vi_adam (later in the stream) reads the
+    // Adam bias corrections 1 / (1 - beta^t) formed here once per iteration
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int t = *t_dev + 1;
+        *t_dev = t;
+        bias[0] = 1.0 / (1.0 - pow(beta1, (double)t));
+        bias[1] = 1.0 / (1.0 - pow(beta2, (double)t));
+    }
     if (r >= R) return;
     const double *mu = phi + (int64_t)r * nphi;
     const double *tri = mu + P;
@@ -57,7 +63,7 @@ __global__ void vi_sample_kernel(const double *phi, const double *eps, int R, in
 
 __global__ void vi_adam_kernel(double *phi, double *m, double *v, const double *eps, const double *g,
                                const double *logp, const double *part, int R, int P, int64_t nphi,
-                               const int32_t *t_dev, double lr, double beta1, double beta2, double eps_adam,
+                               const double *bias, double lr, double beta1, double beta2, double eps_adam,
                                double *elbo)
 {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -71,7 +77,7 @@ __global__ void vi_adam_kernel(double *phi, double *m, double *v, const double *
     } else {
         // packed triangle index -> (i, j): i (i + 1) / 2 <= q < (i + 1) (i + 2) / 2
         const int64_t q = p - P;
-        int i = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+        int i = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f); // corrected below
         while ((int64_t)(i + 1) * (i + 2) / 2 <= q) ++i;
         while ((int64_t)i * (i + 1) / 2 > q) --i;
         const int j = (int)(q - (int64_t)i * (i + 1) / 2);
@@ -82,9 +88,8 @@ __global__ void vi_adam_kernel(double *phi, double *m, double *v, const double *
     const double vv = beta2 * v[idx] + (1.0 - beta2) * grad * grad;
     m[idx] = mm;
     v[idx] = vv;
-    const double t = (double)*t_dev;
-    const double mh = mm / (1.0 - pow(beta1, t));
-    const double vh = vv / (1.0 - pow(beta2, t));
+    const double mh = mm * bias[0];
+    const double vh = vv * bias[1];
     phi[idx] -= lr * mh / (sqrt(vh) + eps_adam);
     if (p == 0 && elbo) elbo[r] = logp[r] + part[r];
 }
@@ -92,22 +97,22 @@ __global__ void vi_adam_kernel(double *phi, double *m, double *v, const double *
 } // namespace
 
 cudaError_t launch_vi_sample(const double *phi, const double *eps, int R, int P, double *u, double *part,
-                             int32_t *t_dev, cudaStream_t st)
+                             int32_t *t_dev, double beta1, double beta2, double *bias, cudaStream_t st)
 {
     if (R == 0) return cudaSuccess;
     const int64_t nphi = (int64_t)P + (int64_t)P * (P + 1) / 2;
-    vi_sample_kernel<<<(R + 3) / 4, 128, 0, st>>>(phi, eps, R, P, nphi, u, part, t_dev);
+    vi_sample_kernel<<<(R + 3) / 4, 128, 0, st>>>(phi, eps, R, P, nphi, u, part, t_dev, beta1, beta2, bias);
     return cudaGetLastError();
 }
 
 cudaError_t launch_vi_adam(double *phi, double *m, double *v, const double *eps, const double *g,
-                           const double *logp, const double *part, int R, int P, const int32_t *t_dev, double lr,
+                           const double *logp, const double *part, int R, int P, const double *bias, double lr,
                            double beta1, double beta2, double eps_adam, double *elbo, cudaStream_t st)
 {
     const int64_t nphi = (int64_t)P + (int64_t)P * (P + 1) / 2;
     const int64_t n = (int64_t)R * nphi;
     if (n == 0) return cudaSuccess;
-    vi_adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(phi, m, v, eps, g, logp, part, R, P, nphi, t_dev,
+    vi_adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(phi, m, v, eps, g, logp, part, R, P, nphi, bias,
                                                                  lr, beta1, beta2, eps_adam, elbo);
     return cudaGetLastError();
 }

@@ -199,3 +199,52 @@ def test_kernel_source_hash_ignores_comments_only(tmp_path, monkeypatch):
     assert bench.kernel_source_hash() == h0
     p.write_text(text + "\nstatic int extra_symbol;\n")
     assert bench.kernel_source_hash() != h0
+
+
+# ------------------------------------------------------- autotune cache ----
+def test_tune_cache_round_trip(tmp_path):
+    import json
+    path = str(tmp_path / "tune.json")
+    key1 = "NVIDIA GB300|152|2|21|12|17|t2"
+    key2 = "NVIDIA GB300|152|0|17|1|13|t2"
+    assert nr.tune_cache_get(path, key1) is None            # no file yet
+    nr.tune_cache_put(path, key1, 1, 12, 4, 134.25)
+    nr.tune_cache_put(path, key2, 0, 6, 7, 0.5)
+    nr.tune_cache_put(path, key1, 1, 6, 3, 130.0)           # replaces the first entry
+    assert nr.tune_cache_get(path, key1) == {"paired": 1, "tile_q": 6, "ctas_per_sm": 3, "ms": 130.0}
+    assert nr.tune_cache_get(path, key2) == {"paired": 0, "tile_q": 6, "ctas_per_sm": 7, "ms": 0.5}
+    assert nr.tune_cache_get(path, "absent|key") is None
+    doc = json.load(open(path))                             # the file is plain JSON
+    assert doc["version"] == 1 and set(doc["entries"]) == {key1, key2}
+    assert doc["entries"][key2] == {"paired": 0, "tile_q": 6, "ctas_per_sm": 7, "ms": 0.5}
+
+
+def test_tune_cache_tolerates_foreign_and_broken_files(tmp_path):
+    import json
+    path = tmp_path / "tune.json"
+    # written by another tool: other field order, extra whitespace
+    path.write_text(json.dumps({"entries": {"k": {"ms": 2.5, "ctas_per_sm": 2, "tile_q": 9, "paired": 0}},
+                                "version": 1}, indent=3))
+    assert nr.tune_cache_get(str(path), "k") == {"paired": 0, "tile_q": 9, "ctas_per_sm": 2, "ms": 2.5}
+    path.write_text("{ not json")
+    assert nr.tune_cache_get(str(path), "k") is None        # unreadable: an empty cache
+    nr.tune_cache_put(str(path), "k2", 1, 3, 1)             # ... which a write replaces
+    assert nr.tune_cache_get(str(path), "k2")["tile_q"] == 3
+    with pytest.raises(nr.NRError):
+        nr.tune_cache_put(str(path), 'bad"key', 1, 3, 1)
+
+
+# --------------------------------------------- strong-scaling partition ----
+def test_cost_partition_covers_every_stack_once_and_balances():
+    from paper_2509_06924_gb300 import shard
+    wl = W.make_workload("uneven", n_stacks=500)
+    q_len = (wl.q_off[1:] - wl.q_off[:-1])[wl.dataset]
+    cost = shard.stack_costs(wl.n_layers, q_len, wl.n_quad)
+    for world in (1, 2, 3, 8):
+        parts = shard.cost_partition(cost, world)
+        allidx = np.sort(np.concatenate(parts))
+        np.testing.assert_array_equal(allidx, np.arange(wl.n_stacks))
+        loads = np.array([cost[p].sum() for p in parts])
+        # LPT greedy: the largest load is within the largest single cost of the mean
+        assert loads.max() <= loads.mean() + cost.max() + 1e-9
+        assert all(np.all(np.diff(p) > 0) for p in parts)

@@ -81,3 +81,96 @@ def test_noalloc_rejects_oversized_and_host_batches():
     cb = hb._c()
     st = lib.nr_loglik_grad_noalloc(ctypes.byref(cb), 17, None, None, None, None)
     assert st == nr.NR_EINVAL
+
+
+def test_noalloc_warm_call_allocates_no_device_memory():
+    # the property the entry point exists for: once the library's module is
+    # loaded, a call changes neither the device's free memory nor torch's
+    # allocator
+    wl = W.make_workload("oled_cofit", n_stacks=8)
+    b = nr.Batch.from_workload(wl)
+    ll = torch.empty(wl.n_stacks, dtype=torch.float64, device="cuda")
+    g = torch.empty(b.params.numel(), dtype=torch.float64, device="cuda")
+    flags = torch.empty(1, dtype=torch.int32, device="cuda")
+    nr.loglik_grad_noalloc(b, wl.n_quad, ll, g, flags)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    a0, r0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    for _ in range(2):
+        nr.loglik_grad_noalloc(b, wl.n_quad, ll, g, flags)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert (torch.cuda.memory_allocated(), torch.cuda.memory_reserved()) == (a0, r0)
+    assert int(flags.item()) == 0 and bool(torch.isfinite(ll).all())
+
+
+def test_noalloc_full_array_matches_nr_loglik_grad():
+    # exactly NR_NOALLOC_MAX_STACKS stacks: the shared array is full
+    S = nr.NOALLOC_MAX_STACKS
+    wl = W.make_workload("thick_oxide", n_stacks=S)
+    b = nr.Batch.from_workload(wl)
+    ll, g, flags = call_noalloc(b, wl.n_quad)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    ll_ref, g_ref = ctx.loglik_grad(b)
+    ll_ref, g_ref = ll_ref.cpu().numpy(), g_ref.cpu().numpy()
+    ctx.close()
+    assert flags == 0
+    assert np.max(np.abs(ll - ll_ref) / np.abs(ll_ref)) <= TOL_LL
+    assert scaled_grad_err(wl, g, g_ref) <= TOL_G
+
+
+def test_noalloc_error_flags_are_cleared_then_raised():
+    lib = nr.load_library()
+    wl = W.make_workload("film_1l", n_stacks=8)
+    bad = wl.r_err.copy()
+    bad[5] = 0.0                                 # e <= 0: NR_FLAG_BAD_ERR, never a trap
+    bb = nr.Batch.from_arrays(wl.n_layers, wl.dataset, wl.q_off, wl.params, wl.q, wl.dq, wl.r_obs, bad)
+    _, _, flags = call_noalloc(bb, wl.n_quad)
+    assert flags & nr.NR_FLAG_BAD_ERR
+    # without a flags buffer the status goes to the library's own word and the
+    # call still succeeds
+    ll = torch.empty(wl.n_stacks, dtype=torch.float64, device="cuda")
+    cb = bb._c()
+    st = lib.nr_loglik_grad_noalloc(ctypes.byref(cb), wl.n_quad, ctypes.c_void_p(ll.data_ptr()), None, None,
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == nr.NR_OK
+    torch.cuda.synchronize()
+    # a clean batch afterwards: the flags word starts at zero again
+    ll, g, flags = call_noalloc(nr.Batch.from_workload(wl), wl.n_quad)
+    assert flags == 0 and np.all(np.isfinite(ll)) and np.all(np.isfinite(g))
+
+
+def test_noalloc_refuses_stream_capture():
+    lib = nr.load_library()
+    wl = W.make_workload("film_1l", n_stacks=4)
+    b = nr.Batch.from_workload(wl)
+    call_noalloc(b, wl.n_quad)                   # set-up on this device, eager
+    ll = torch.empty(wl.n_stacks, dtype=torch.float64, device="cuda")
+    cb = b._c()
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        ll.zero_()                               # the graph holds something
+        st = lib.nr_loglik_grad_noalloc(ctypes.byref(cb), wl.n_quad, ctypes.c_void_p(ll.data_ptr()), None, None,
+                                        ctypes.c_void_p(s.cuda_stream))
+    assert st == nr.NR_EINVAL
+    assert b"captured" in lib.nr_last_error()
+    # the library and the device stay usable
+    ll2, _, flags = call_noalloc(b, wl.n_quad)
+    assert flags == 0 and np.all(np.isfinite(ll2))
+
+
+def test_noalloc_binding_checks_output_buffers():
+    wl = W.make_workload("film_1l", n_stacks=4)
+    b = nr.Batch.from_workload(wl)
+    short = torch.empty(wl.n_stacks - 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        nr.loglik_grad_noalloc(b, wl.n_quad, short, None)
+    with pytest.raises(ValueError):
+        nr.loglik_grad_noalloc(b, wl.n_quad, None, torch.empty(b.params.numel(), dtype=torch.float32,
+                                                               device="cuda"))
+    ll = torch.empty(wl.n_stacks, dtype=torch.float64, device="cuda")
+    nr.loglik_grad_noalloc(b, wl.n_quad, ll, None)  # either output may be left out
+    torch.cuda.synchronize()
+    assert bool(torch.isfinite(ll).all())
