@@ -378,7 +378,7 @@ def cpu_baseline(wl, target_s: float = 10.0, gpu=None, fd=None) -> dict:
         m_ref = oracle.batch("model", sub.n_layers, sub.params, sub.dataset, sub.q_off, sub.q, sub.dq, None, None,
                              sub.n_quad)
         acc = {"mixed": accuracy(wl, count, gpu["ll"], gpu["g"], gpu.get("m"), ll_ref, g_ref, m_ref),
-               "bounds": {"log_model_abs": 1e-5, "loglik_rel": 1e-5, "grad_scaled": 1e-4}}
+               "bounds": {"log_model_abs": 2e-5, "loglik_rel": 1e-5, "grad_scaled": 1e-4}}
         if fd is not None:
             k = min(count, fd[0].size)
             acc["fp64_fd"] = accuracy(wl, k, fd[0], fd[1], None, ll_ref, g_ref)

@@ -310,6 +310,11 @@ typedef struct nr_cofit_model {
     const int32_t *slot_src;  /* [sum_c (4 n_c + 6)] HOST: k in [0, P) or -1    */
     const double *slot_val;   /* [same] HOST: value of the fixed slots          */
     const double *lo, *hi;    /* [P] HOST: prior bounds, finite, lo < hi        */
+    int32_t res_param;        /* free parameter k that scales every dQ of every
+                                 contrast (dQ_i -> theta_k dQ_i: a shared
+                                 resolution / smearing percentage, Sec. 4.2;
+                                 its gradient comes from the resolution
+                                 derivative of nr_loglik_grad_res); -1: none  */
 } nr_cofit_model;
 
 typedef struct nr_sampler nr_sampler;

@@ -14,6 +14,10 @@ Sampling runs in the unconstrained coordinates u:
     log pi(u) = sum_c loglik_c(theta(u)) + sum_k [log s_k + log(1 - s_k)],
 the second sum being the uniform prior density times the Jacobian of the
 map (up to the constant sum_k log(hi_k - lo_k) - log(hi_k - lo_k) = 0).
+Optionally one free parameter (res_param) is a resolution scale f shared by
+every contrast: each dataset's dQ_i becomes f dQ_i (the shared smearing
+percentage of the LED co-fit, Sec. 4.2, is such an f when dQ_i = Q_i), and
+d loglik / d f = (d loglik / d ln f) / f from the resolution derivative.
 
 One step from u0 with standard-normal draws z (one per parameter) and a
 uniform draw U (as log U), diagonal inverse mass m^-1, step eps, L steps:
@@ -35,7 +39,7 @@ class Model:
     concatenated packed blocks; lo/hi: per free parameter; data: (q_off, Q,
     dQ, Robs, err) shared by all chains; K quadrature nodes."""
 
-    def __init__(self, n_layers, dataset, slot_src, slot_val, lo, hi, q_off, Q, dQ, Robs, err, K):
+    def __init__(self, n_layers, dataset, slot_src, slot_val, lo, hi, q_off, Q, dQ, Robs, err, K, res_param=-1):
         self.n_layers = np.asarray(n_layers, np.int32)
         self.dataset = np.asarray(dataset, np.int32)
         self.slot_src = np.asarray(slot_src, np.int64)
@@ -47,6 +51,8 @@ class Model:
         self.Robs, self.err = np.asarray(Robs, np.float64), np.asarray(err, np.float64)
         self.K = int(K)
         self.P = self.lo.size
+        self.res_param = int(res_param)
+        assert -1 <= self.res_param < self.P
         self.n_slots = int(np.sum(4 * self.n_layers + 6))
         assert self.slot_src.size == self.n_slots == self.slot_val.size
 
@@ -67,9 +73,15 @@ class Model:
         th, s = self.theta(u)
         p = self.packed(u)
         C = self.n_layers.size
-        ll, g = oracle.batch("grad", self.n_layers, p, self.dataset, self.q_off, self.Q, self.dQ, self.Robs,
-                             self.err, self.K)
         gt = np.zeros(self.P)                         # d loglik / d theta, tied slots summed
+        if self.res_param >= 0:
+            f = th[self.res_param]
+            ll, g, gres = oracle.batch("grad_res", self.n_layers, p, self.dataset, self.q_off, self.Q,
+                                       f * self.dQ, self.Robs, self.err, self.K)
+            gt[self.res_param] = np.sum(gres) / f
+        else:
+            ll, g = oracle.batch("grad", self.n_layers, p, self.dataset, self.q_off, self.Q, self.dQ, self.Robs,
+                                 self.err, self.K)
         tied = self.slot_src >= 0
         np.add.at(gt, self.slot_src[tied], g[tied])
         # log s + log(1 - s) = -|u| - 2 log(1 + e^-|u|)

@@ -66,7 +66,8 @@ class CCofitModel(ctypes.Structure):
                 ("n_layers", ctypes.c_void_p), ("dataset", ctypes.c_void_p), ("n_datasets", ctypes.c_int32),
                 ("q_off", ctypes.c_void_p), ("q", ctypes.c_void_p), ("dq", ctypes.c_void_p),
                 ("r_obs", ctypes.c_void_p), ("r_err", ctypes.c_void_p), ("slot_src", ctypes.c_void_p),
-                ("slot_val", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p)]
+                ("slot_val", ctypes.c_void_p), ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p),
+                ("res_param", ctypes.c_int32)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -359,11 +360,12 @@ class Sampler:
     nr_hmc_step).  Per contrast: n_layers, dataset (index into the datasets
     given by q_off and the device tensors q, dq, r_obs, r_err); per packed
     slot of the concatenated contrasts: slot_src (free parameter or -1) and
-    slot_val (fixed value); per free parameter: uniform prior bounds lo, hi.
+    slot_val (fixed value); per free parameter: uniform prior bounds lo, hi;
+    res_param: the free parameter that scales every dQ (-1: none).
     States u are unconstrained: theta = lo + (hi - lo) sigmoid(u)."""
 
     def __init__(self, ctx: Context, n_chains: int, n_layers, dataset, q_off, q, dq, r_obs, r_err, slot_src,
-                 slot_val, lo, hi):
+                 slot_val, lo, hi, res_param: int = -1):
         import numpy as np
         self._lib = ctx._lib
         self._ctx = ctx                                   # the sampler lives in the context
@@ -376,7 +378,7 @@ class Sampler:
         self.n_chains, self.n_free = int(n_chains), int(lo_.size)
         m = CCofitModel(self.n_chains, nl.size, self.n_free, nl.ctypes.data, ds.ctypes.data, qo.size - 1,
                         qo.ctypes.data, q.data_ptr(), dq.data_ptr(), r_obs.data_ptr(), r_err.data_ptr(),
-                        src.ctypes.data, val.ctypes.data, lo_.ctypes.data, hi_.ctypes.data)
+                        src.ctypes.data, val.ctypes.data, lo_.ctypes.data, hi_.ctypes.data, int(res_param))
         h = ctypes.c_void_p()
         _check(self._lib.nr_sampler_create(ctx._h, ctypes.byref(m), ctypes.byref(h)))
         self._h = h

@@ -261,6 +261,8 @@ struct nr_sampler {
     DevBuf d_src, d_val, d_lo, d_hi, d_tie_ptr, d_tie_slot, d_params, d_ll, d_gpk, d_mom, d_u0, d_H0, d_lp0;
     DevBuf d_vu, d_vg, d_vlp, d_vpart; // variational step: u = mu + L e, d log pi / du, log pi, ELBO part
     DevBuf d_vbias;                    // Adam bias corrections of the current iteration (2 doubles)
+    int res_param = -1;                // free parameter scaling every dQ (-1: none)
+    DevBuf d_dqs, d_gres;              // per stack: that scale, d loglik / d ln(scale)
 };
 
 namespace {
@@ -537,10 +539,11 @@ nr_status get_plan(nr_ctx *ctx, const nr_batch *b, int mode, Plan **out)
 }
 
 nr_status launch_device(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, float *r_out, double *ll,
-                        double *grad, double *gres, cudaStream_t st)
+                        double *grad, double *gres, cudaStream_t st, const double *dq_scale = nullptr)
 {
     if (pl.S == 0) return NR_OK;
     KernelArgs a{};
+    a.dq_scale = dq_scale;
     a.params = b->params;
     a.q = b->q;
     a.dq = b->dq;
@@ -779,7 +782,7 @@ nr_status run_host(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, float *r_
 }
 
 nr_status compute(nr_ctx *ctx, const nr_batch *b, int mode, float *r_out, double *ll, double *grad, double *gres,
-                  void *stream)
+                  void *stream, const double *dq_scale = nullptr)
 {
     static const char *const kNames[] = {"nr_reflectivity", "nr_loglik", "nr_loglik_grad", "nr_loglik_grad_res"};
     NvtxRange range(kNames[mode]);
@@ -797,7 +800,7 @@ nr_status compute(nr_ctx *ctx, const nr_batch *b, int mode, float *r_out, double
     if (st != NR_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (b->memory == NR_MEM_HOST) return run_host(ctx, *pl, b, mode, r_out, ll, grad, gres, s);
-    return launch_device(ctx, *pl, b, mode, r_out, ll, grad, gres, s);
+    return launch_device(ctx, *pl, b, mode, r_out, ll, grad, gres, s, dq_scale);
 }
 
 } // namespace
@@ -962,6 +965,11 @@ nr_status nr_sampler_create(nr_ctx *ctx, const nr_cofit_model *m, nr_sampler **o
     for (int k = 0; k < P; ++k)
         if (!std::isfinite(m->lo[k]) || !std::isfinite(m->hi[k]) || !(m->lo[k] < m->hi[k]))
             return fail(NR_EINVAL, "parameter %d: bounds [%g, %g]", k, m->lo[k], m->hi[k]);
+    if (m->res_param < -1 || m->res_param >= P)
+        return fail(NR_EINVAL, "res_param %d outside [-1, %d)", m->res_param, P);
+    if (m->res_param >= 0 && !(m->lo[m->res_param] > 0.0))
+        return fail(NR_EINVAL, "resolution scale parameter %d: lower bound %g not positive", m->res_param,
+                    m->lo[m->res_param]);
     std::vector<int32_t> tie_ptr(P + 1, 0), tie_slot;
     for (int i = 0; i < NS; ++i) {
         const int k = m->slot_src[i];
@@ -1012,6 +1020,11 @@ nr_status nr_sampler_create(nr_ctx *ctx, const nr_cofit_model *m, nr_sampler **o
     NR_CUDA(S.d_vlp.ensure(sizeof(double) * C));
     NR_CUDA(S.d_vpart.ensure(sizeof(double) * C));
     NR_CUDA(S.d_vbias.ensure(sizeof(double) * 2));
+    S.res_param = m->res_param;
+    if (S.res_param >= 0) {
+        NR_CUDA(S.d_dqs.ensure(sizeof(double) * (size_t)C * NC));
+        NR_CUDA(S.d_gres.ensure(sizeof(double) * (size_t)C * NC));
+    }
     NR_CUDA(cudaMemcpy(S.d_src.p, m->slot_src, sizeof(int32_t) * NS, cudaMemcpyHostToDevice));
     NR_CUDA(cudaMemcpy(S.d_val.p, m->slot_val, sizeof(double) * NS, cudaMemcpyHostToDevice));
     NR_CUDA(cudaMemcpy(S.d_lo.p, m->lo, sizeof(double) * P, cudaMemcpyHostToDevice));
@@ -1069,6 +1082,8 @@ CofitStageArgs stage_args(nr_sampler *S, double *u, int stage)
     a.u0 = S->d_u0.as<double>();
     a.H0 = S->d_H0.as<double>();
     a.logp0 = S->d_lp0.as<double>();
+    a.res_param = S->res_param;
+    a.gres = S->d_gres.as<double>();
     return a;
 }
 
@@ -1076,8 +1091,12 @@ CofitStageArgs stage_args(nr_sampler *S, double *u, int stage)
 nr_status sampler_eval(nr_sampler *S, const double *u, cudaStream_t st)
 {
     cudaError_t e = launch_cofit_gather(u, S->C, S->P, S->NS, S->d_src.as<int32_t>(), S->d_val.as<double>(),
-                                        S->d_lo.as<double>(), S->d_hi.as<double>(), S->d_params.as<double>(), st);
+                                        S->d_lo.as<double>(), S->d_hi.as<double>(), S->d_params.as<double>(),
+                                        S->res_param, S->NC, S->d_dqs.as<double>(), st);
     if (e != cudaSuccess) return fail(NR_ECUDA, "sampler gather: %s", cudaGetErrorString(e));
+    if (S->res_param >= 0)
+        return compute(S->ctx, &S->batch, kGradRes, nullptr, S->d_ll.as<double>(), S->d_gpk.as<double>(),
+                       S->d_gres.as<double>(), st, S->d_dqs.as<double>());
     return compute(S->ctx, &S->batch, kGrad, nullptr, S->d_ll.as<double>(), S->d_gpk.as<double>(), nullptr, st);
 }
 } // namespace

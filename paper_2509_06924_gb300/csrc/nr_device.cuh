@@ -83,9 +83,10 @@ __device__ __forceinline__ void sincos_approx(float x, float &sn, float &cs)
 // the table keeps within the tolerance where the special-function unit did
 // not.
 #ifndef NR_SINCOS_TABLE
-#define NR_SINCOS_TABLE 0
+#define NR_SINCOS_TABLE 1
 #endif
-// the same choice for the Nevot-Croce factors (defaults to the phases')
+// the same choice for the Nevot-Croce factors (their phase is usually small,
+// but the special-function unit's error there is absolute too)
 #ifndef NR_NC_TABLE
 #define NR_NC_TABLE NR_SINCOS_TABLE
 #endif

@@ -14,7 +14,8 @@
 // The likelihood and its gradient come from the mixed gradient kernel.  The
 // kernels here are the glue of a step, all chain-parallel and FP64 (the
 // arrays are tiny next to the likelihood):
-//   cofit_gather: u -> packed parameters of every stack;
+//   cofit_gather: u -> packed parameters of every stack (and the chain's
+//                 resolution scale f for its stacks, when one is sampled);
 //   cofit_stage:  one warp per chain pulls the packed gradient back to u
 //                 (tied slots summed, chain rule through the sigmoid, prior
 //                 term), reduces log pi, and applies the leapfrog stage:
@@ -35,11 +36,17 @@ namespace {
 constexpr unsigned kFullMask = 0xffffffffu;
 
 __global__ void cofit_gather_kernel(const double *u, int C, int P, int NS, const int32_t *src, const double *val,
-                                    const double *lo, const double *hi, double *params)
+                                    const double *lo, const double *hi, double *params, int res_param, int NC,
+                                    double *dq_scale)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)C * NS) return;
     const int c = (int)(i / NS), slot = (int)(i - (int64_t)c * NS);
+    if (res_param >= 0 && slot < NC) {
+        // the chain's resolution scale, for each of its NC stacks
+        const double s = 1.0 / (1.0 + exp(-u[(int64_t)c * P + res_param]));
+        dq_scale[(int64_t)c * NC + slot] = lo[res_param] + (hi[res_param] - lo[res_param]) * s;
+    }
     const int k = src[slot];
     double v = val[slot];
     if (k >= 0) {
@@ -78,6 +85,13 @@ __global__ void cofit_stage_kernel(CofitStageArgs a)
         lp += -au - 2.0 * log1p(exp(-au));
         double gt = 0.0;
         for (int t = a.tie_ptr[k]; t < a.tie_ptr[k + 1]; ++t) gt += gpk[a.tie_slot[t]];
+        if (k == a.res_param) {
+            // d loglik / d f = (d loglik / d ln f) / f, summed over the contrasts
+            const double f = a.lo[k] + (a.hi[k] - a.lo[k]) * s;
+            double gr = 0.0;
+            for (int i = 0; i < a.n_contrast; ++i) gr += a.gres[(int64_t)c * a.n_contrast + i];
+            gt += gr / f;
+        }
         const double g = gt * (a.hi[k] - a.lo[k]) * s * (1.0 - s) + (1.0 - 2.0 * s);
         if (a.stage == kStageLogp) {
             if (a.grad_out) a.grad_out[(int64_t)c * P + k] = g;
@@ -132,11 +146,13 @@ __global__ void cofit_stage_kernel(CofitStageArgs a)
 } // namespace
 
 cudaError_t launch_cofit_gather(const double *u, int C, int P, int NS, const int32_t *src, const double *val,
-                                const double *lo, const double *hi, double *params, cudaStream_t st)
+                                const double *lo, const double *hi, double *params, int res_param, int NC,
+                                double *dq_scale, cudaStream_t st)
 {
     const int64_t n = (int64_t)C * NS;
     if (n == 0) return cudaSuccess;
-    cofit_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, C, P, NS, src, val, lo, hi, params);
+    cofit_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(u, C, P, NS, src, val, lo, hi, params,
+                                                                     res_param, NC, dq_scale);
     return cudaGetLastError();
 }
 

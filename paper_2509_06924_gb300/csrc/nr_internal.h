@@ -76,6 +76,7 @@ struct KernelArgs {
     int32_t *stack_done; // per-stack arrival counters (self-resetting)
     int32_t *ticket;     // [2]: next work item, finished CTAs (self-resetting)
     int32_t *status;     // sticky NR_FLAG_* word
+    const double *dq_scale; // [n_stacks] factor of every dQ of the stack's dataset (NULL: 1)
     // FP64 plain path only
     double *ll_pert;     // [(chunk slots) * n_pert] partial chi^2 sums per perturbation
     int32_t n_pert;      // 1, or 2 * max(4n+6) + 1 for central differences
@@ -134,12 +135,16 @@ struct CofitStageArgs {
     double *mom;                  // [C x P] momentum (workspace)
     double *u0;                   // [C x P] starting position (workspace)
     double *H0, *logp0;           // [C] (workspace)
+    int32_t res_param;            // free parameter scaling every dQ (-1: none)
+    const double *gres;           // [C x n_contrast] d loglik / d ln f of the stacks (res_param >= 0)
     double *logp_out;             // [C] log pi of the resulting state (may be NULL)
     double *grad_out;             // [C x P] d log pi / du (kStageLogp; may be NULL)
     int32_t *accepted;            // [C] 1 accepted, 0 rejected (may be NULL)
 };
+// res_param >= 0: also dq_scale[c * NC + i] = theta_res of chain c (its NC stacks)
 cudaError_t launch_cofit_gather(const double *u, int C, int P, int NS, const int32_t *src, const double *val,
-                                const double *lo, const double *hi, double *params, cudaStream_t st);
+                                const double *lo, const double *hi, double *params, int res_param, int NC,
+                                double *dq_scale, cudaStream_t st);
 cudaError_t launch_cofit_stage(const CofitStageArgs &a, cudaStream_t st);
 // variational inference (nr_vi.cu)
 // vi_sample advances the device iteration counter and writes the Adam bias

@@ -266,6 +266,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
         // super-tile are summed with full warps when the next one is staged
         // (and after the last tile), not by one lane per Q point per tile.
         const float *qp = ka.q + si.q_begin, *dqp = ka.dq + si.q_begin;
+        const float fsc = ka.dq_scale ? (float)ka.dq_scale[wi.stack] : 1.f; // resolution scale of the stack
         const float *rop = ka.r_obs + si.q_begin, *rep = ka.r_err + si.q_begin;
         const int span = (T::CAPQ / TQ) * TQ;
         int sb = wi.q_lo;     // first Q point of the staged super-tile
@@ -297,7 +298,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                 float4 v = make_float4(0.05f, 0.f, 0.f, 0.f);
                 if (qa < wi.q_hi) {
                     v.x = 0.5f * __ldg(qp + qa);
-                    v.y = 0.5f * __ldg(dqp + qa);
+                    v.y = 0.5f * fsc * __ldg(dqp + qa);
                     if (LIK) {
                         v.z = __ldg(rop + qa);
                         v.w = rcp_approx(__ldg(rep + qa));

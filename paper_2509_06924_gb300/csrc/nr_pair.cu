@@ -490,6 +490,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
         // per-thread sums of the loglik terms, d/dscale, d/dbkg (per Q point)
         float ll_hi = 0.f, ll_lo = 0.f, gsc_acc = 0.f, gbk_acc = 0.f;
         const float *qp = ka.q + si.q_begin, *dqp = ka.dq + si.q_begin;
+        const float fsc = ka.dq_scale ? (float)ka.dq_scale[wi.stack] : 1.f; // resolution scale of the stack
         const float *rop = ka.r_obs + si.q_begin, *rep = ka.r_err + si.q_begin;
         const int span = (CAPQ / TQ) * TQ;
         int sb = wi.q_lo, s_next = wi.q_lo, s_cnt = 0;
@@ -517,7 +518,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                 float4 v = make_float4(0.05f, 0.f, 0.f, 0.f); // past the end: a harmless node, 1/err = 0
                 if (qa < wi.q_hi) {
                     v.x = 0.5f * __ldg(qp + qa);
-                    v.y = 0.5f * __ldg(dqp + qa);
+                    v.y = 0.5f * fsc * __ldg(dqp + qa);
                     if constexpr (LIK) {
                         v.z = __ldg(rop + qa);
                         v.w = rcp_approx(__ldg(rep + qa));

@@ -61,8 +61,22 @@ def small_model(seed=7):
     return hmc.Model([n, n], [0, 1], slot_src, slot_val, lo, hi, q_off, Qa, dQ, Robs, 0.05 * m, 17), u_t
 
 
-def test_unconstrained_gradient_matches_central_differences():
+def with_resolution(model, lo=0.6, hi=1.4):
+    """The same model with one more free parameter: a resolution scale f of
+    every dQ (both contrasts), prior [lo, hi]."""
+    import oracle
+    mod = hmc.Model(model.n_layers, model.dataset, model.slot_src, model.slot_val, np.append(model.lo, lo),
+                    np.append(model.hi, hi), model.q_off, model.Q, model.dQ, model.Robs, model.err, model.K,
+                    res_param=model.P)
+    return mod
+
+
+@pytest.mark.parametrize("res", [False, True])
+def test_unconstrained_gradient_matches_central_differences(res):
     model, u_t = small_model()
+    if res:
+        model = with_resolution(model)
+        u_t = np.append(u_t, 0.4)
     u = u_t + 0.3
     lp, g = model.logp_grad(u)
     for k in range(model.P):
@@ -71,6 +85,22 @@ def test_unconstrained_gradient_matches_central_differences():
         e[k] = h
         fd = (model.logp_grad(u + e)[0] - model.logp_grad(u - e)[0]) / (2 * h)
         assert abs(fd - g[k]) <= 1e-5 * max(1.0, abs(g[k]))
+
+
+def test_resolution_parameter_scales_every_dq():
+    """log pi with a free resolution scale f equals the model without it,
+    evaluated on the data with every dQ multiplied by f, plus the prior
+    term of f."""
+    model, u_t = small_model()
+    mres = with_resolution(model)
+    for uf in (-1.2, 0.0, 0.7):
+        f = 0.6 + 0.8 / (1.0 + np.exp(-uf))
+        lp, _ = mres.logp_grad(np.append(u_t, uf))
+        scaled = hmc.Model(model.n_layers, model.dataset, model.slot_src, model.slot_val, model.lo, model.hi,
+                           model.q_off, model.Q, f * model.dQ, model.Robs, model.err, model.K)
+        lp0, _ = scaled.logp_grad(u_t)
+        prior_f = -abs(uf) - 2.0 * np.log1p(np.exp(-abs(uf)))
+        assert abs(lp - (lp0 + prior_f)) <= 1e-12 * abs(lp)
 
 
 def test_packed_slots_tie_and_fix():

@@ -2,13 +2,22 @@
 same seeded inputs, element by element.
 
 Tolerances (per stack):
-  smeared model m:   max |log m - log m_ref|              <= 1e-5
+  smeared model m:   max |log m - log m_ref|              <= 2e-5
   log-likelihood:    |l - l_ref| / |l_ref|                <= 1e-5
   gradient:          ||(g - g_ref) * typ||_inf / ||g_ref * typ||_inf <= 1e-4
 with typ = (1 A, 1e-6 A^-2, 1e-8 A^-2, 1 A, 1, 1e-7) per parameter class
-(the pre-scaling advice of Sec. 2.3.1).  The plain FP64 path is held to
-1e-12 (log-likelihood), FP32 rounding of its float output (model) and 1e-5
-(its central-difference gradient).
+(the pre-scaling advice of Sec. 2.3.1).  The model bound is twice the
+log-likelihood's: a quadrature node within about 0.1 % (in k^2) of an
+interior layer's critical edge loses digits to the cancellation of the
+Parratt step above that layer (relative error ~ u k_0 / |k_j|), which the
+smeared value keeps in part while the sum over Q points of the likelihood
+averages it away.  A stack whose exact results move
+by more than these bounds / 8 when its inputs are perturbed by one FP32
+unit roundoff (oracle.perturbation_floor: an ill-conditioned stack, e.g.
+a waveguide resonance sampled at its peak) is held to 8 times that response
+instead: an FP32 evaluation cannot land closer than its own roundings allow.
+The plain FP64 path is held to 1e-12 (log-likelihood), FP32 rounding of its
+float output (model) and 1e-5 (its central-difference gradient).
 """
 import ctypes
 import os
@@ -24,7 +33,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-TOL_M, TOL_LL, TOL_G = 1e-5, 1e-5, 1e-4
+TOL_M, TOL_LL, TOL_G = 2e-5, 1e-5, 1e-4
+COND = 8.0  # headroom over the oracle's own response to FP32-size input perturbations
 
 
 def run_gpu(wl, precision="mixed", modes=("model", "loglik", "grad"), **kw):
@@ -65,20 +75,50 @@ def grad_err(wl, g, g_ref, stacks=None):
     return worst
 
 
-def assert_parity(wl, gpu, ref, tol_m=TOL_M, tol_ll=TOL_LL, tol_g=TOL_G):
-    assert gpu["flags"] == 0
+def stack_errors(wl, gpu, ref):
+    """Per-stack errors of the outputs present in both gpu and ref:
+    'model' max |log m - log m_ref|, 'loglik' and 'loglik_g' (the gradient
+    call's) |l - l_ref| / |l_ref|, 'grad' the scaled gradient error."""
+    S = wl.n_stacks
+    out = {}
     if "m" in gpu and "m" in ref:
         assert np.all(np.isfinite(gpu["m"]))
-        e = np.max(np.abs(np.log(gpu["m"]) - np.log(ref["m"]))) if gpu["m"].size else 0.0
-        assert e <= tol_m, f"model: max |dlog m| {e:.3e}"
-    if "ll" in gpu:
-        e = np.max(np.abs(gpu["ll"] - ref["ll"]) / np.maximum(np.abs(ref["ll"]), 1e-300))
-        assert e <= tol_ll, f"loglik: rel {e:.3e}"
-    if "g" in gpu:
-        e = np.max(np.abs(gpu["ll_g"] - ref["ll"]) / np.maximum(np.abs(ref["ll"]), 1e-300))
-        assert e <= tol_ll, f"loglik (grad call): rel {e:.3e}"
-        e = grad_err(wl, gpu["g"], ref["g"])
-        assert e <= tol_g, f"gradient: scaled {e:.3e}"
+        e = np.abs(np.log(gpu["m"]) - np.log(ref["m"]))
+        oo = wl.out_off
+        out["model"] = np.array([e[oo[s]:oo[s + 1]].max() if oo[s + 1] > oo[s] else 0.0 for s in range(S)])
+    if "ll" in gpu and "ll" in ref:
+        out["loglik"] = np.abs(gpu["ll"] - ref["ll"]) / np.maximum(np.abs(ref["ll"]), 1e-300)
+    if "g" in gpu and "g" in ref:
+        out["loglik_g"] = np.abs(gpu["ll_g"] - ref["ll"]) / np.maximum(np.abs(ref["ll"]), 1e-300)
+        out["grad"] = np.array([grad_err(wl, gpu["g"], ref["g"], [s]) for s in range(S)])
+    return out
+
+
+FLOOR_OF = {"model": "model", "loglik": "loglik", "loglik_g": "loglik", "grad": "grad"}
+
+
+def check_bounds(wl, errs, tol):
+    """Every stack within its base bound tol[kind], or, where the stack is
+    ill-conditioned, within COND times the oracle's response to FP32-size
+    input perturbations (computed for the stacks over the base bound only)."""
+    over = sorted({s for k, e in errs.items() for s in np.flatnonzero(e > tol[k])})
+    if not over:
+        return
+    sub = wl.subset(over)
+    typ = np.concatenate([W.typical_scale(int(n)) for n in sub.n_layers])
+    fl = oracle.perturbation_floor(sub.n_layers, sub.params, sub.dataset, sub.q_off, sub.q, sub.dq, sub.r_obs,
+                                   sub.r_err, sub.n_quad, typ)
+    for i, s in enumerate(over):
+        for k, e in errs.items():
+            bound = max(tol[k], COND * fl[FLOOR_OF[k]][i])
+            assert e[s] <= bound, (f"stack {s} {k}: error {e[s]:.3e} above {tol[k]:.0e} and above {COND:g} x its "
+                                   f"FP32 perturbation floor {fl[FLOOR_OF[k]][i]:.3e}")
+
+
+def assert_parity(wl, gpu, ref, tol_m=TOL_M, tol_ll=TOL_LL, tol_g=TOL_G):
+    assert gpu["flags"] == 0
+    errs = stack_errors(wl, gpu, ref)
+    check_bounds(wl, errs, {"model": tol_m, "loglik": tol_ll, "loglik_g": tol_ll, "grad": tol_g})
 
 
 # ------------------------------------------------------------ workloads ----
@@ -121,14 +161,21 @@ def test_mixed_parity_full_size_sampled(name, samples):
     rng = np.random.default_rng(20250906)
     stacks = np.sort(rng.choice(wl.n_stacks, size=min(samples, wl.n_stacks), replace=False))
     sub = wl.subset(stacks)
-    ref = run_oracle(sub, modes=("grad",))
-    po = wl.par_off
-    g = np.concatenate([gpu["g"][po[s]:po[s + 1]] for s in stacks])
-    ll = gpu["ll_g"][stacks]
-    assert np.max(np.abs(ll - ref["ll"]) / np.abs(ref["ll"])) <= TOL_LL
-    # the forward-only call (its own kernels) at the same stacks
-    assert np.max(np.abs(gpu["ll"][stacks] - ref["ll"]) / np.abs(ref["ll"])) <= TOL_LL
-    assert grad_err(sub, g, ref["g"]) <= TOL_G
+    ref = run_oracle(sub, modes=("model", "grad"))
+    po, oo = wl.par_off, wl.out_off
+    # the smeared model of the whole batch (nr_reflectivity), the sampled
+    # stacks' slices taken on the device
+    ctx = nr.Context(n_quad=wl.n_quad)
+    m_all = ctx.reflectivity(nr.Batch.from_workload(wl))
+    idx = torch.as_tensor(np.concatenate([np.arange(oo[s], oo[s + 1]) for s in stacks]), device=m_all.device)
+    m = m_all[idx].cpu().numpy().astype(np.float64)
+    assert ctx.device_status() == 0
+    ctx.close()
+    del m_all
+    sel = {"m": m, "ll": gpu["ll"][stacks], "ll_g": gpu["ll_g"][stacks],
+           "g": np.concatenate([gpu["g"][po[s]:po[s + 1]] for s in stacks])}
+    check_bounds(sub, stack_errors(sub, sel, ref), {"model": TOL_M, "loglik": TOL_LL, "loglik_g": TOL_LL,
+                                                   "grad": TOL_G})
     # a property that holds for every stack: only SLD differences matter,
     # so d/d rho_0 = -sum_j d/d rho_j
     for s in range(0, wl.n_stacks, max(1, wl.n_stacks // 4096)):
@@ -199,14 +246,13 @@ def test_deep_stacks_every_bucket():
 
 
 def test_stacks_deeper_than_the_workloads():
-    """21..64 layers (beyond every workload): the FP32 recursion error grows
-    with depth, so the model and loglik bounds scale as 1e-5 * n / 20 there."""
+    """21..64 layers (beyond every workload), under the same bounds."""
     rng = np.random.default_rng(4)
     grid = (W.log_grid(77, 0.005, 0.25), 0.05 * W.log_grid(77, 0.005, 0.25))
     ns = [21, 33, 64]
     stacks = [(n, rand_stack(rng, n, d_range=(5, 60)), 0) for n in ns]
     wl = custom_workload(stacks, [grid])
-    assert_parity(wl, run_gpu(wl), run_oracle(wl), tol_m=TOL_M * 64 / 20, tol_ll=TOL_LL * 64 / 20)
+    assert_parity(wl, run_gpu(wl), run_oracle(wl))
 
 
 def test_empty_and_ragged_datasets():
@@ -505,27 +551,35 @@ def test_sld_profile_sharp_steps_host_batch_and_flags():
 
 
 # ------------------------------------------------------- on-device HMC step
-def sampler_setup(C=8, seed=7):
+def sampler_setup(C=8, seed=7, res=False):
+    """A two-contrast co-fit sampler and its CPU reference; res: one more
+    free parameter, the resolution scale f of every dQ (prior [0.6, 1.4])."""
     import sys
     sys.path.insert(0, os.path.dirname(__file__))
-    from test_oracle_hmc import small_model
+    from test_oracle_hmc import small_model, with_resolution
     from oracle import hmc
     model, u_t = small_model(seed)
+    if res:
+        model = with_resolution(model)
+        u_t = np.append(u_t, 0.4)
     # the device holds the data as float32: the reference uses the same values
     f32 = lambda a: np.asarray(a, np.float32)
     ref = hmc.Model(model.n_layers, model.dataset, model.slot_src, model.slot_val, model.lo, model.hi,
-                    model.q_off, f32(model.Q), f32(model.dQ), f32(model.Robs), f32(model.err), model.K)
+                    model.q_off, f32(model.Q), f32(model.dQ), f32(model.Robs), f32(model.err), model.K,
+                    res_param=model.res_param)
     ctx = nr.Context(n_quad=model.K)
     dev = lambda a: torch.as_tensor(f32(a), device="cuda")
     smp = nr.Sampler(ctx, C, model.n_layers, model.dataset, model.q_off, dev(model.Q), dev(model.dQ),
-                     dev(model.Robs), dev(model.err), model.slot_src, model.slot_val, model.lo, model.hi)
+                     dev(model.Robs), dev(model.err), model.slot_src, model.slot_val, model.lo, model.hi,
+                     res_param=model.res_param)
     rng = np.random.default_rng(seed + 1)
     u = u_t[None, :] + 0.2 * rng.normal(size=(C, model.P))
     return ctx, smp, ref, u, rng
 
 
-def test_sampler_logp_grad_parity():
-    ctx, smp, ref, u, _ = sampler_setup()
+@pytest.mark.parametrize("res", [False, True])
+def test_sampler_logp_grad_parity(res):
+    ctx, smp, ref, u, _ = sampler_setup(res=res)
     lp, g = smp.logp_grad(torch.as_tensor(u, device="cuda"))
     lp, g = lp.cpu().numpy(), g.cpu().numpy()
     for c in range(u.shape[0]):
@@ -536,9 +590,10 @@ def test_sampler_logp_grad_parity():
     ctx.close()
 
 
-def test_hmc_step_parity_and_graph_replay():
+@pytest.mark.parametrize("res", [False, True])
+def test_hmc_step_parity_and_graph_replay(res):
     C, P_eps, L = 8, 4e-4, 6
-    ctx, smp, ref, u, rng = sampler_setup(C)
+    ctx, smp, ref, u, rng = sampler_setup(C, res=res)
     z = rng.normal(size=(C, ref.P))
     inv_mass = np.full(ref.P, 1.0)
     # first half of the chains must accept, the rest reject: decisions that
@@ -618,7 +673,9 @@ def test_vi_step_parity_and_graph_replay():
         # the gradient carries the mixed path's ~1e-5 relative error; Adam's
         # step is lr * mhat / sqrt(vhat): its error stays a small fraction of lr
         np.testing.assert_allclose(ph[r], np.concatenate([mu_r, tri_r]), rtol=0, atol=2e-3 * 0.05)
-        np.testing.assert_allclose(m[r], m_r, rtol=1e-4, atol=1e-9 * np.max(np.abs(m_r)))
+        # Adam's first moment carries the gradient's error: held to the
+        # gradient bound, 1e-4 of the largest gradient term (1 - beta1) g
+        assert np.max(np.abs(m[r] - m_r)) <= 1e-4 * np.max(np.abs(m_r - 0.9 * m0[r]))
     # a captured iteration replays with the device counter advancing
     ph2, m2, v2, t2, e2 = dev(phi), dev(m0), dev(v0), dev(np.array([t0], np.int32)), dev(eps)
     s = torch.cuda.Stream()
