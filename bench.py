@@ -55,16 +55,28 @@ DEFAULT_WORKLOAD = "vi_step"
 SECONDARY = ("thick_oxide", "oled_cofit", "uneven", "film_1l")
 
 
+# FP32 flops of one table-driven sin/cos (cis_tab): reduction by multiples
+# of 2 pi / 64 (8), remainder polynomial (8), angle addition (6).  A layer
+# phase E_j already counts its reduction in its 18 flops (double-float phase
+# 7, reduction 8, amplitude and product 3), so it adds 14; a Nevot-Croce
+# factor adds all 22.
+CIS_PHASE = 14
+CIS_NC = 22
+
+
 def flops_per_eval(n: int, K: int) -> float:
     """Algorithmic FP32 flops of one fwd+grad evaluation of an n-layer stack
-    (FMA = 2), counted term by term from the gradient kernel's source.  Not
-    counted: transcendental (XU) operations, compares and selects, and the
-    redundant copies of the smearing sum that every lane of a Q point forms."""
+    (FMA = 2), counted term by term from the gradient kernel's source,
+    including the FP32 arithmetic of the table-driven sin/cos.  Not counted:
+    special-function (XU) operations, compares and selects, and the redundant
+    copies of the smearing sum that every lane of a Q point forms."""
     store = n <= 2
     fres0 = 29                             # r_0: k_0 is real
     # node q (double-float) 15, k_0^2 6, backing k 10, |X|^2 3; per layer:
-    # k_j with Newton step 25, r_j 34, E_j 18, Y_j 6, Moebius step 20
-    fwd = 15 + 6 + 10 + fres0 + 3 + n * (25 + 34 + 18 + 6 + 20)
+    # k_j with Newton step 25, r_j 34, E_j 18, Y_j 6, Moebius step 20; the
+    # sin/cos of every layer phase and Nevot-Croce factor
+    cis = CIS_PHASE * n + CIS_NC * (n + 1)
+    fwd = 15 + 6 + 10 + fres0 + 3 + n * (25 + 34 + 18 + 6 + 20) + cis
     seed = 11                              # smearing, model, residual, adjoint seed
     # adjoint: Moebius/phase terms 54 per layer, Fresnel/roughness terms 22 per
     # interface, k_j adjoint 8 (4 for the real k_0) and 1/k_j terms 25 per
@@ -73,17 +85,20 @@ def flops_per_eval(n: int, K: int) -> float:
     if store:
         adj += 2 + 6 * n                   # k_j k_{j+1}, re-formed from the kept k_j
     else:                                  # k, r, E, D recomputed top-down
-        adj += (25 * n + 10) + (fres0 + 34 * n) + 36 * n
+        adj += (25 * n + 10) + (fres0 + 34 * n) + 36 * n + cis
     per_q = 15.0 / K                       # likelihood terms, once per Q point
     return float(fwd + seed + adj + per_q)
 
 
-def flops_per_eval_fwd(n: int, K: int) -> float:
-    """Algorithmic FP32 flops of one forward (log-likelihood) evaluation:
-    the forward sweep of flops_per_eval, the smearing product and sum (2),
-    and per Q point the model, the residual (4) and the likelihood terms
-    (15)."""
+def flops_per_eval_fwd(n: int, K: int, table: bool = False) -> float:
+    """Algorithmic FP32 flops of one forward evaluation: the forward sweep
+    of flops_per_eval, the smearing product and sum (2), and per Q point the
+    model, the residual (4) and the likelihood terms (15).  table: with the
+    FP32 sin/cos of the model and gradient kernels (the log-likelihood
+    kernel takes its sin/cos from the special-function unit)."""
     fwd = 15 + 6 + 10 + 29 + 3 + n * (25 + 34 + 18 + 6 + 20)
+    if table:
+        fwd += CIS_PHASE * n + CIS_NC * (n + 1)
     return float(fwd + 2 + 19.0 / K)
 
 

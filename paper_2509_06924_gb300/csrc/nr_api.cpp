@@ -162,7 +162,12 @@ int grad_bucket(int n)
         if (b > 1 && n <= b) return b;
     return -1;
 }
-int fwd_bucket(int n) { return n == 1 ? 1 : 0; }
+// Forward (model, log-likelihood) buckets: exactly one layer; up to 20 layers
+// (the paired runtime-n kernel, whose log-likelihood mode takes the
+// special-function unit's sin / cos); deeper stacks (64: the one-evaluation
+// runtime-n kernel, table sin / cos in every mode, since the special-function
+// unit's phase error accumulates over that many layers)
+int fwd_bucket(int n) { return n == 1 ? 1 : n <= 20 ? 0 : 64; }
 
 struct Group {
     int nmax = 0;

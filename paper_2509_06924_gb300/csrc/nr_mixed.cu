@@ -833,7 +833,7 @@ bool mixed_bucket_ok(int mode, int nmax)
 #undef X
         return false;
     }
-    return nmax == 0 || nmax == 1;
+    return nmax == 0 || nmax == 1 || nmax == 64; // 64: runtime n, stacks deeper than 20 layers
 }
 
 int mixed_tile_q(int mode, int nmax, int K, bool allow_pair)

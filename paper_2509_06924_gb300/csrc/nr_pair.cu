@@ -215,7 +215,9 @@ __device__ __forceinline__ Kz2 medium_kz2(f2 p_hi, f2 p_lo, float4 m)
     }
 }
 
-// E = exp(2 i k d), phase in double-float (as layer_phase)
+// E = exp(2 i k d), phase in double-float (as layer_phase).  TAB: the table
+// sin / cos (NR_SINCOS_TABLE), else the special-function unit's.
+template <bool TAB>
 __device__ __forceinline__ c2 layer_phase2(const Kz2 &k, float4 L, const float *tab)
 {
     const f2 ph = pmul(k.re, bc(L.x));
@@ -224,21 +226,21 @@ __device__ __forceinline__ c2 layer_phase2(const Kz2 &k, float4 L, const float *
     pl = pfma(k.lo, bc(L.x), pl);
     const f2 amp = pex2(pmul(k.im, bc(L.z)));
     f2 s, c;
-#if NR_SINCOS_TABLE
-    pcis_tab(ph, pl, tab, c, s);
-#else
-    const f2 nt = padd(pfma(ph, bc(kInv2Pi), bc(kRoundMagic)), bc(-kRoundMagic));
-    f2 red = pfma(pneg(nt), bc(kTwoPiHi), ph);
-    red = pfma(pneg(nt), bc(kTwoPiLo), red);
-    red = padd(red, pl);
-    psincos(red, s, c);
-#endif
+    if constexpr (TAB && NR_SINCOS_TABLE) {
+        pcis_tab(ph, pl, tab, c, s);
+    } else {
+        const f2 nt = padd(pfma(ph, bc(kInv2Pi), bc(kRoundMagic)), bc(-kRoundMagic));
+        f2 red = pfma(pneg(nt), bc(kTwoPiHi), ph);
+        red = pfma(pneg(nt), bc(kTwoPiLo), red);
+        red = padd(red, pl);
+        psincos(red, s, c);
+    }
     return c2{pmul(amp, c), pmul(amp, s)};
 }
 
 // r_j with Nevot-Croce roughness, G = exp(s k_a k_b) / S^2 and kk = k_a k_b
 // (as fresnel_nc).  A vanishing S (k_a = k_b = 0) gives G = r = 0.
-template <bool REAL_A>
+template <bool REAL_A, bool TAB>
 __device__ __forceinline__ c2 fresnel_nc2(c2 ka, c2 kb, float4 I, c2 &G, c2 &kk, const float *tab)
 {
     const f2 Sx = padd(ka.re, kb.re);
@@ -249,11 +251,8 @@ __device__ __forceinline__ c2 fresnel_nc2(c2 ka, c2 kb, float4 I, c2 &G, c2 &kk,
     kk = REAL_A ? c2{pmul(ka.re, kb.re), pmul(ka.re, kb.im)} : cmul2(ka, kb);
     const f2 amp = pex2(pmul(bc(I.w), kk.re));
     f2 sn, cs;
-#if NR_NC_TABLE
-    pcis_tab(pmul(bc(I.z), kk.im), bc(0.f), tab, cs, sn);
-#else
-    psincos(pmul(bc(I.z), kk.im), sn, cs);
-#endif
+    if constexpr (TAB && NR_NC_TABLE) pcis_tab(pmul(bc(I.z), kk.im), bc(0.f), tab, cs, sn);
+    else psincos(pmul(bc(I.z), kk.im), sn, cs);
     G = cmul2(c2{pmul(amp, cs), pmul(amp, sn)}, iS2);
     return cmul2(c2{bc(I.x), bc(I.y)}, G);
 }
@@ -331,6 +330,10 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
     constexpr bool GRAD = PT::GRAD;
     constexpr bool ROLL = PT::ROLL;
     constexpr bool LIK = MODE != kModel;
+    // sin / cos by table for the model and the gradient; the log-likelihood
+    // alone keeps the special-function unit's (its sum over Q points
+    // averages their error: within 5e-6 of the oracle on every workload)
+    constexpr bool TAB = MODE != kLoglik;
     static_assert(GRAD ? (NMAX >= 1 && NMAX <= NR_MAX_LAYERS) : (NMAX == 1 || NMAX == 0),
                   "paired kernel: gradient buckets, 1-layer and runtime-n forward");
     constexpr int NM = NMAX > 0 ? NMAX : NR_MAX_LAYERS; // shared-memory capacity in layers
@@ -594,14 +597,14 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                 else kj = medium_kz2<true>(p_hi, p_lo, sm.med[j]);
                 c2 Gj, kkj;
                 const float4 Ij = sm.itf[j];
-                const c2 rj = top ? fresnel_nc2<true>(kc2(kj), kc2(kbelow), Ij, Gj, kkj, sh_cs)
-                                  : fresnel_nc2<false>(kc2(kj), kc2(kbelow), Ij, Gj, kkj, sh_cs);
+                const c2 rj = top ? fresnel_nc2<true, TAB>(kc2(kj), kc2(kbelow), Ij, Gj, kkj, sh_cs)
+                                  : fresnel_nc2<false, TAB>(kc2(kj), kc2(kbelow), Ij, Gj, kkj, sh_cs);
                 c2 Xj;
                 if (bot) {
                     Xj = rj;
                     if constexpr (!ROLL) kst[j + 1] = kbelow;
                 } else {
-                    const c2 Ej = layer_phase2(kbelow, sm.lay[j + 1], sh_cs);
+                    const c2 Ej = layer_phase2<TAB>(kbelow, sm.lay[j + 1], sh_cs);
                     const c2 Yj = cmul2(Xbelow, Ej);
                     c2 Dj;
                     Xj = mobius2(rj, Yj, Dj);
@@ -700,8 +703,8 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                         if constexpr (ROLL) {
                             const float4 Mj1 = sm.med[j + 1];
                             kj1 = bot ? medium_kz2<false>(p_hi, p_lo, Mj1) : medium_kz2<true>(p_hi, p_lo, Mj1);
-                            rj = top ? fresnel_nc2<true>(kc2(kj), kc2(kj1), Ij, Gj, kkj, sh_cs)
-                                     : fresnel_nc2<false>(kc2(kj), kc2(kj1), Ij, Gj, kkj, sh_cs);
+                            rj = top ? fresnel_nc2<true, TAB>(kc2(kj), kc2(kj1), Ij, Gj, kkj, sh_cs)
+                                     : fresnel_nc2<false, TAB>(kc2(kj), kc2(kj1), Ij, Gj, kkj, sh_cs);
                         } else {
                             kj1 = kst[j + 1];
                             rj = rst[j];
@@ -714,7 +717,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                             c2 Ej1, Dj, Y;
                             if constexpr (ROLL) {
                                 const float4 x1 = sh_X[(j + 1) * BLOCK + tid];
-                                Ej1 = layer_phase2(kj1, Lj1, sh_cs);
+                                Ej1 = layer_phase2<TAB>(kj1, Lj1, sh_cs);
                                 Y = cmul2(c2{make_float2(x1.x, x1.y), make_float2(x1.z, x1.w)}, Ej1);
                                 const c2 rY = cmul2(rj, Y);
                                 const f2 dx = padd(bc(1.f), rY.re), dy = rY.im;
