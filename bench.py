@@ -105,8 +105,9 @@ def flops_per_eval_fwd(n: int, K: int, table: bool = False) -> float:
 def workload_flops(wl, per_eval) -> float:
     """Sum over stacks of per_eval(n, K) x the stack's evaluations."""
     oo = wl.out_off
-    return float(sum(per_eval(int(n), wl.n_quad) * (oo[s + 1] - oo[s]) * wl.n_quad
-                     for s, n in enumerate(wl.n_layers)))
+    evals = (oo[1:] - oo[:-1]) * wl.n_quad
+    table = {int(n): per_eval(int(n), wl.n_quad) for n in np.unique(wl.n_layers)}
+    return float(sum(table[int(n)] * float(e) for n, e in zip(wl.n_layers, evals)))
 
 
 def sm_count(dev) -> int:
@@ -401,6 +402,22 @@ def cpu_baseline(wl, target_s: float = 10.0, gpu=None, fd=None) -> dict:
     return out
 
 
+def secondary_accuracy(W, samples: dict) -> dict:
+    """The other workloads' first stacks (outputs kept by measure_config)
+    against the oracle: part of the oracle leg."""
+    import oracle
+    res = {}
+    for name, smp in samples.items():
+        wl = W.make_workload(name)
+        sub = wl.subset(np.arange(smp["stacks"]))
+        ll_ref, g_ref = oracle.batch("grad", sub.n_layers, sub.params, sub.dataset, sub.q_off, sub.q, sub.dq,
+                                     sub.r_obs, sub.r_err, sub.n_quad)
+        m_ref = oracle.batch("model", sub.n_layers, sub.params, sub.dataset, sub.q_off, sub.q, sub.dq, None, None,
+                             sub.n_quad)
+        res[name] = accuracy(sub, sub.n_stacks, smp["ll"], smp["g"], smp["m"], ll_ref, g_ref, m_ref)
+    return res
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle (the only other implementation of the
     method here), timed per step on a bounded sample of the workload."""
@@ -656,30 +673,70 @@ def time_device(fn, steps: int, flush, stream) -> float:
     return sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / steps
 
 
+ACC_SAMPLE = {"thick_oxide": 48, "film_1l": 48, "oled_cofit": 24, "uneven": 24}
+
+
 def measure_config(nr, W, name: str, dev, flush, stream, peak_flops: float, steps: int = 10) -> dict:
     """fwd+grad and forward (log-likelihood) throughput of another workload,
     each call timed like the headline step (L2 flushed, CUDA events), with
     its flop-count fraction of the measured FP32 peak.  The one-layer film
-    (the plain-FP64-forward workload) also times the FP64 forward."""
+    (the plain-FP64-forward workload) also times the FP64 forward.  The
+    uneven batch is planned by the autotuner, through a tune-cache file: a
+    first context tunes and writes the cache, a second reads it (both plan
+    times and the chosen launch shapes are reported).  Returns the first
+    stacks' outputs as well (key "_out"), for the oracle leg's accuracy."""
     import torch
     wl = W.make_workload(name)
-    ctx = nr.Context(n_quad=wl.n_quad)
     b = nr.Batch.from_workload(wl, device=dev)
-    ctx.plan(b)
+    tune = None
+    if name == "uneven":
+        fd, cache = tempfile.mkstemp(suffix=".json")
+        os.close(fd)
+        os.unlink(cache)
+        old = os.environ.get("NR_TUNE_CACHE")
+        os.environ["NR_TUNE_CACHE"] = cache
+        try:
+            t0 = time.perf_counter()
+            c0 = nr.Context(n_quad=wl.n_quad, autotune=True)
+            c0.plan(b)
+            t_tune = time.perf_counter() - t0
+            c0.close()
+            t0 = time.perf_counter()
+            ctx = nr.Context(n_quad=wl.n_quad, autotune=True)
+            ctx.plan(b)
+            t_cached = time.perf_counter() - t0
+            entries = len(json.load(open(cache))["entries"])
+        finally:
+            if old is None:
+                os.environ.pop("NR_TUNE_CACHE", None)
+            else:
+                os.environ["NR_TUNE_CACHE"] = old
+            if os.path.exists(cache):
+                os.unlink(cache)
+        tune = {"plan_s_tuning": t_tune, "plan_s_from_cache": t_cached, "cache_entries": entries,
+                "groups": ctx.plan_groups(b, grad=True)}
+    else:
+        ctx = nr.Context(n_quad=wl.n_quad)
+        ctx.plan(b)
     info = ctx.plan_info(b)
     ll = torch.empty(wl.n_stacks, dtype=torch.float64, device=dev)
     g = torch.empty(b.params.numel(), dtype=torch.float64, device=dev)
     ms_g = time_device(lambda: ctx.loglik_grad(b, ll_out=ll, grad_out=g, stream=stream), steps, flush, stream)
+    k = min(ACC_SAMPLE.get(name, 16), wl.n_stacks)
+    sample = {"ll": ll[:k].cpu().numpy(), "g": g[:int(wl.par_off[k])].cpu().numpy(),
+              "m": ctx.reflectivity(b)[:int(wl.out_off[k])].cpu().numpy(), "stacks": k}
     ms_f = time_device(lambda: ctx.loglik(b, out=ll, stream=stream), steps, flush, stream)
     status = ctx.device_status()
     ctx.close()
     fl_g, fl_f = workload_flops(wl, flops_per_eval), workload_flops(wl, flops_per_eval_fwd)
     out = {"stacks": wl.n_stacks, "evals_per_call": wl.evals, "layers": sorted(set(int(x) for x in wl.n_layers)),
            "fwd_grad": {"value": wl.evals / (ms_g * 1e-3), "ms_per_call": ms_g,
-                        "frac": fl_g / (ms_g * 1e-3) / peak_flops},
+                        "frac": fl_g / (ms_g * 1e-3) / peak_flops, "flops_per_eval": fl_g / wl.evals},
            "loglik": {"value": wl.evals / (ms_f * 1e-3), "ms_per_call": ms_f,
-                      "frac": fl_f / (ms_f * 1e-3) / peak_flops},
-           "launches_per_call": info["launches"], "steps": steps, "device_flags": status}
+                      "frac": fl_f / (ms_f * 1e-3) / peak_flops, "flops_per_eval": fl_f / wl.evals},
+           "launches_per_call": info["launches"], "steps": steps, "device_flags": status, "_out": sample}
+    if tune is not None:
+        out["autotune"] = tune
     if name == "film_1l":
         c64 = nr.Context(n_quad=wl.n_quad, precision="fp64")
         c64.plan(b)
@@ -811,8 +868,8 @@ def run_ours(args):
 
     flops = workload_flops(wl, flops_per_eval)
     # layer-evaluations weight each evaluation by its interface count n + 1
-    layer_evals = sum((int(n) + 1) * (wl.out_off[s + 1] - wl.out_off[s]) * wl.n_quad
-                      for s, n in enumerate(wl.n_layers))
+    oo = wl.out_off
+    layer_evals = int(np.sum((wl.n_layers.astype(np.int64) + 1) * (oo[1:] - oo[:-1]))) * wl.n_quad
     kernel_ms = ms_rank  # the step is one launch of the gradient kernel per layer bucket
     achieved = flops / (kernel_ms * 1e-3)
     prof = profile_record(args.workload)
@@ -856,9 +913,11 @@ def run_ours(args):
                               "frac": evals / (kernel_ms * 1e-3) * ope / lane_peak,
                               "basis": "FP32 lane operations per evaluation counted by ncu (FFMA/FADD/FMUL, "
                                        "paired FFMA2/FADD2/FMUL2 counted twice) over the measured FMA lane rate"}
+    samples = {}
     if ws == 1 and not args.no_infer:
         line["secondary"] = {nm: measure_config(nr, W, nm, dev, flush, stream, peak_fp32)
                              for nm in SECONDARY if nm != args.workload}
+        samples = {nm: v.pop("_out") for nm, v in line["secondary"].items()}
         line["hmc"] = hmc_measure(nr, W, dev)
         line["vi"] = vi_measure(nr, W, dev)
         line["vi_step_graph"] = vi_step_measure(nr, W, dev)
@@ -867,6 +926,8 @@ def run_ours(args):
         gpu = {"ll": ll.cpu().numpy(), "g": g.cpu().numpy(), "m": m_out.cpu().numpy()}
         cb = cpu_baseline(wl, gpu=gpu, fd=fd)
         line["accuracy"] = cb.pop("_accuracy")
+        if samples:
+            line["accuracy"]["secondary"] = secondary_accuracy(W, samples)
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     if ws > 1:

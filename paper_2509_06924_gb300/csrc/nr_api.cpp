@@ -227,10 +227,10 @@ bool make_quad_const(int K, QuadConst &qc)
         qc.wd[k] = w[k] * isp;
         qc.w[k] = (float)(w[k] * isp);
     }
-    for (int i = 0; i < 64; ++i) {
-        const double a = 2.0 * M_PI * i / 64.0;
+    for (int i = 0; i < kSinCosTabN; ++i) {
+        const double a = 2.0 * M_PI * i / kSinCosTabN;
         qc.cs_tab[i] = (float)std::cos(a);
-        qc.cs_tab[64 + i] = (float)std::sin(a);
+        qc.cs_tab[kSinCosTabN + i] = (float)std::sin(a);
     }
     return true;
 }

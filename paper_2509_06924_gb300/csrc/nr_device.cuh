@@ -91,7 +91,8 @@ __device__ __forceinline__ void sincos_approx(float x, float &sn, float &cs)
 #define NR_NC_TABLE NR_SINCOS_TABLE
 #endif
 
-constexpr int kTabN = 64;
+constexpr int kTabN = kSinCosTabN;
+static_assert(kTabN == 64, "reduction constants are for 64 entries");
 constexpr float kTabScale = 10.18591594696045f;      // 64 / (2 pi)
 constexpr float kTabStepHi = 0.09817477315664291f;   // float(2 pi / 64)
 constexpr float kTabStepLo = -2.7319617679211206e-09f; // 2 pi / 64 - kTabStepHi

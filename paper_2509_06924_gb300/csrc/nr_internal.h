@@ -39,6 +39,9 @@ struct WorkItem {
     int32_t chunk; // index among the stack's items (partial-sum slot)
 };
 
+// Entries of the kernels' sin / cos table (a power of two)
+constexpr int kSinCosTabN = 64;
+
 // Quadrature rule as the kernels use it: node offset q = Q + dQ * g_k with
 // g_k = x_k / (2 sqrt(ln 2)) as a float pair (hi + lo) and as a double, and
 // weight w_k / sqrt(pi).
@@ -48,9 +51,9 @@ struct QuadConst {
     float w[NR_MAX_QUAD];
     double gd[NR_MAX_QUAD];
     double wd[NR_MAX_QUAD];
-    // cos(2 pi i / 64) at [i], sin at [64 + i], i < 64, correctly rounded:
-    // the table of the kernels' sin / cos (nr_device.cuh, cis_tab)
-    float cs_tab[128];
+    // cos(2 pi i / N) at [i], sin at [N + i], i < N = kSinCosTabN, correctly
+    // rounded: the table of the kernels' sin / cos (nr_device.cuh, cis_tab)
+    float cs_tab[2 * kSinCosTabN];
     int32_t K;
 };
 

@@ -713,3 +713,49 @@ def test_autotuned_plan_keeps_parity(name, S):
     gpu["flags"] = ctx.device_status()
     ctx.close()
     assert_parity(wl, gpu, run_oracle(wl))
+
+
+# ------------------------------------------------- failure injection ------
+def test_alloc_failure_leaves_context_usable():
+    """An allocation failure (injected on the host: nr_debug_fail_allocs,
+    no cudaMalloc is called) surfaces as NR_ENOMEM, and the same context
+    completes the plan and the call afterwards."""
+    wl = W.make_workload("oled_cofit", n_stacks=4)
+    try:
+        nr.debug_fail_allocs(1)                # the context's status word
+        with pytest.raises(nr.NRError) as err:
+            nr.Context(n_quad=wl.n_quad)
+        assert err.value.status == nr.NR_ENOMEM
+        nr.debug_fail_allocs(0)
+        ctx = nr.Context(n_quad=wl.n_quad)
+        b = nr.Batch.from_workload(wl)
+        nr.debug_fail_allocs(2)                # the new plan's work-list buffers
+        with pytest.raises(nr.NRError) as err:
+            ctx.loglik_grad(b)
+        assert err.value.status == nr.NR_ENOMEM
+    finally:
+        nr.debug_fail_allocs(0)
+    ll, g = ctx.loglik_grad(b)
+    assert ctx.device_status() == 0
+    ref = run_oracle(wl, modes=("grad",))
+    assert np.max(np.abs(ll.cpu().numpy() - ref["ll"]) / np.abs(ref["ll"])) <= TOL_LL
+    assert grad_err(wl, g.cpu().numpy(), ref["g"]) <= TOL_G
+    ctx.close()
+
+
+def test_waveguide_resonance_stacks():
+    """A 520-700 A low-SLD layer between two 300 A high-SLD layers guides
+    neutrons between the critical edges of its neighbours: sharp resonances
+    whose gradient is most sensitive to rounding (the first stack's exact
+    gradient moves by 7e-5 of its largest component under one-unit-roundoff
+    input perturbations).  Dense Q over the guided range, 21 nodes; the
+    scaled gradient error must stay within 5e-5 here, half the general bound."""
+    q = W.log_grid(160, 0.006, 0.03)
+    stacks = []
+    for d_core, rho_hi in ((600.0, 6.0e-6), (600.0, 5.3e-6), (520.0, 6.3e-6), (700.0, 5.8e-6)):
+        stacks.append((3, W.pack([300.0, d_core, 300.0], [0.0, rho_hi, 1.0e-6, rho_hi, 2.07e-6],
+                                 [1e-9, 2e-10, 1e-9, 0.0], [4.0, 3.0, 3.0, 5.0], 1.0, 1e-7), 0))
+    wl = custom_workload(stacks, [(q, 0.05 * q)], K=21)
+    gpu, ref = run_gpu(wl), run_oracle(wl)
+    assert_parity(wl, gpu, ref)
+    assert grad_err(wl, gpu["g"], ref["g"]) <= 5e-5
