@@ -86,6 +86,9 @@ typedef enum { NR_MEM_DEVICE = 0, NR_MEM_HOST = 1 } nr_memory;
 #define NR_FLAG_NONFINITE_PARAM 1 /* a parameter was NaN/Inf                 */
 #define NR_FLAG_BAD_Q 2           /* a quadrature node fell at q <= 0        */
 #define NR_FLAG_BAD_ERR 4         /* an uncertainty e_i was <= 0 or NaN      */
+#define NR_FLAG_DEBUG_BOUNDS 8    /* NR_DEBUG builds only: a kernel met a work
+                                     item or queue slot outside its buffers
+                                     and skipped it (its outputs are invalid) */
 
 typedef struct nr_options {
     int32_t n_quad;        /* K quadrature nodes (default 17 when 0)          */
@@ -390,6 +393,16 @@ nr_status nr_vi_step(nr_sampler *sampler, double *phi, double *adam_m, double *a
  * NR_ENOMEM and leaves the context usable.  0 disarms.  Process-wide.
  * ---------------------------------------------------------------------- */
 nr_status nr_debug_fail_allocs(int32_t count);
+
+/* Testing hook of NR_DEBUG builds (release builds return NR_EINVAL): with
+ * on = 1, the first work item of the batch's gradient plan (planned by this
+ * call if needed) is given a stack index one past the batch, as a corrupted
+ * plan would hold; the next gradient call's kernels must report
+ * NR_FLAG_DEBUG_BOUNDS and skip that item (its stack's outputs are then
+ * invalid) instead of reading outside the stack array.  on = 0 restores the
+ * item and clears the plan's per-stack arrival counters, after which the plan
+ * computes correctly again.  Synchronous. */
+nr_status nr_debug_poison_plan(nr_ctx *ctx, const nr_batch *batch, int32_t on);
 
 #ifdef __cplusplus
 }

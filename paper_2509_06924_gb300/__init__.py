@@ -29,14 +29,14 @@ from . import _build
 NR_OK, NR_EINVAL, NR_ENOMEM, NR_ECUDA, NR_ETIMEOUT, NR_ENONFINITE = range(6)
 NR_MIXED, NR_FP64_PLAIN = 0, 1
 NR_MEM_DEVICE, NR_MEM_HOST = 0, 1
-NR_FLAG_NONFINITE_PARAM, NR_FLAG_BAD_Q, NR_FLAG_BAD_ERR = 1, 2, 4
+NR_FLAG_NONFINITE_PARAM, NR_FLAG_BAD_Q, NR_FLAG_BAD_ERR, NR_FLAG_DEBUG_BOUNDS = 1, 2, 4, 8
 MAX_LAYERS = 64
 MAX_QUAD = 32
 EXPORTS = ("nr_create", "nr_destroy", "nr_last_error", "nr_plan", "nr_reflectivity", "nr_loglik",
            "nr_loglik_grad", "nr_loglik_grad_res", "nr_sld_profile", "nr_device_status", "nr_quadrature",
            "nr_plan_info", "nr_loglik_grad_noalloc", "nr_sampler_create", "nr_sampler_destroy",
            "nr_sampler_logp_grad", "nr_hmc_step", "nr_vi_step", "nr_plan_groups", "nr_tune_cache_get",
-           "nr_tune_cache_put", "nr_debug_fail_allocs")
+           "nr_tune_cache_put", "nr_debug_fail_allocs", "nr_debug_poison_plan")
 NOALLOC_MAX_STACKS = 16384
 
 
@@ -84,20 +84,28 @@ _LIB = None
 _LIB_LOCK = threading.Lock()
 
 
+def debug_build_selected() -> bool:
+    """NR_DEBUG=1 in the environment selects the NR_DEBUG library (device
+    bounds checks that set NR_FLAG_DEBUG_BOUNDS) for this process."""
+    return os.environ.get("NR_DEBUG") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.DEBUG_LIB if debug_build_selected() else _build.LIB
 
 
 def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Load libnr.so (building it first when it is missing or stale)."""
+    """Load libnr.so, or its NR_DEBUG variant (building it first when it is
+    missing or stale)."""
     global _LIB
     with _LIB_LOCK:
         if _LIB is None:
+            path = library_path()
             if build_if_missing:
-                _build.build()
-            if not os.path.exists(_build.LIB):
-                raise RuntimeError(f"the CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
-            lib = ctypes.CDLL(_build.LIB)
+                _build.build_debug() if debug_build_selected() else _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"the CUDA library {path} is missing; run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
             vp, i32, i64p = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)
             i32p = ctypes.POINTER(ctypes.c_int32)
             dp = ctypes.POINTER(ctypes.c_double)
@@ -128,6 +136,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
             lib.nr_tune_cache_get.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(TuneEntry)]
             lib.nr_tune_cache_put.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(TuneEntry)]
             lib.nr_debug_fail_allocs.argtypes = [i32]
+            lib.nr_debug_poison_plan.argtypes = [vp, ctypes.POINTER(CBatch), i32]
             for name in EXPORTS:
                 if name not in ("nr_destroy", "nr_last_error", "nr_sampler_destroy"):
                     getattr(lib, name).restype = ctypes.c_int
@@ -345,6 +354,13 @@ class Context:
                                         ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(iota.data_ptr()),
                                         _stream_handle(stream)))
         return rho.view(batch.n_stacks, nz), iota.view(batch.n_stacks, nz)
+
+    def debug_poison_plan(self, batch: Batch, on: bool) -> None:
+        """Testing hook of NR_DEBUG builds (nr_debug_poison_plan): corrupt
+        (on) or restore (off) the first work item of the batch's gradient
+        plan."""
+        cb = batch._c()
+        _check(self._lib.nr_debug_poison_plan(self._h, ctypes.byref(cb), int(bool(on))))
 
     def device_status(self, stream=None) -> int:
         """Synchronise and return (and clear) the sticky NR_FLAG_* word."""

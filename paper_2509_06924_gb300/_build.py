@@ -1,8 +1,10 @@
 """Builds the C-ABI library ``_build/libnr.so`` in-tree for sm_103a with
 nvcc (kernels) and g++ (host API), compiling the translation units in
-parallel, and the arithmetic-pipe probes ``_build/libnr_peak.so`` that the
-benchmark measures its roofline denominators with.  No CMake, no torch
-extension machinery."""
+parallel, the arithmetic-pipe probes ``_build/libnr_peak.so`` that the
+benchmark measures its roofline denominators with, and on request the
+NR_DEBUG variant ``_build/debug/libnr_debug.so`` (device bounds checks that
+report instead of trapping; the binding loads it when NR_DEBUG=1).  No
+CMake, no torch extension machinery."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -16,6 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libnr.so")
 PEAK_LIB = os.path.join(OUT_DIR, "libnr_peak.so")
+DEBUG_LIB = os.path.join(OUT_DIR, "debug", "libnr_debug.so")
 PEAK_SOURCE = "nr_peak.cu"
 INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -38,10 +41,10 @@ def _nvcc() -> str:
     return os.path.join(_cuda_home(), "bin", "nvcc")
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in CU_SOURCES + CPP_SOURCES + HEADERS]
     deps += [os.path.join(INCLUDE, "nr.h"), os.path.abspath(__file__)]
     return any(os.path.getmtime(d) > t for d in deps)
@@ -80,7 +83,7 @@ def build(force: bool = False, verbose: bool = False, defines=None, out: str | N
     for src in CPP_SOURCES:
         obj = os.path.join(out_dir, src + ".o")
         objs.append(obj)
-        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", *inc, "-I", cuda_inc, "-c",
+        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", *dflags, *inc, "-I", cuda_inc, "-c",
                      os.path.join(CSRC_, src), "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         results = list(ex.map(_run, jobs))
@@ -91,6 +94,13 @@ def build(force: bool = False, verbose: bool = False, defines=None, out: str | N
     _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"])
     os.replace(tmp, lib_path)
     return lib_path
+
+
+def build_debug(force: bool = False) -> str:
+    """Compile (if needed) and return the path of the NR_DEBUG library."""
+    if not force and not _stale(DEBUG_LIB):
+        return DEBUG_LIB
+    return build(defines={"NR_DEBUG": 1}, out=DEBUG_LIB)
 
 
 def build_peak(force: bool = False) -> str:

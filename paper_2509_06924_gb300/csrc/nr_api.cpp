@@ -252,6 +252,7 @@ struct nr_ctx {
     // host-memory staging
     DevBuf s_params, s_q, s_dq, s_robs, s_rerr, s_out, s_ll, s_grad, s_res;
     DevBuf p_off, p_nl, p_z, p_rho, p_iota; // SLD-profile metadata and host-call staging
+    WorkItem poisoned{-1, 0, 0, 0};         // nr_debug_poison_plan: the item it replaced
 };
 
 // On-device HMC sampler: the replicated likelihood batch of C chains x
@@ -559,6 +560,7 @@ nr_status launch_device(nr_ctx *ctx, Plan &pl, const nr_batch *b, int mode, floa
     a.grad_out = grad;
     a.res_out = gres;
     a.status = ctx->d_status;
+    a.n_stacks = pl.S;
     if (ctx->opt.precision == NR_FP64_PLAIN) {
         a.stacks = pl.d64_stacks.as<StackInfo>();
         a.items = pl.d64_items.as<WorkItem>();
@@ -653,6 +655,7 @@ nr_status autotune_worklist(nr_ctx *ctx, Plan &pl, const nr_batch *b, bool grad)
     a.ll_out = ll.as<double>();
     a.grad_out = gr.as<double>();
     a.status = ctx->d_status;
+    a.n_stacks = pl.S;
     a.stacks = wl.d_stacks.as<StackInfo>();
     a.partials = wl.d_partials.as<double>();
     a.stack_done = wl.d_done.as<int32_t>();
@@ -1215,6 +1218,38 @@ nr_status nr_debug_fail_allocs(int32_t count)
 {
     if (count < 0) return fail(NR_EINVAL, "count < 0");
     g_fail_allocs.store(count);
+    return NR_OK;
+}
+
+nr_status nr_debug_poison_plan(nr_ctx *ctx, const nr_batch *batch, int32_t on)
+{
+    if (!NR_DEBUG) return fail(NR_EINVAL, "nr_debug_poison_plan needs a library built with NR_DEBUG");
+    if (!ctx) return fail(NR_EINVAL, "context is NULL");
+    if (on != 0 && on != 1) return fail(NR_EINVAL, "on must be 0 or 1");
+    if (ctx->opt.precision != NR_MIXED) return fail(NR_EINVAL, "the hook corrupts NR_MIXED plans only");
+    nr_status st = validate(batch);
+    if (st != NR_OK) return st;
+    if (batch->memory != NR_MEM_DEVICE) return fail(NR_EINVAL, "the hook takes a device batch");
+    NR_CUDA(cudaSetDevice(ctx->device));
+    Plan *pl = nullptr;
+    st = get_plan(ctx, batch, kGrad, &pl);
+    if (st != NR_OK) return st;
+    WorkList &wl = pl->grad;
+    if (wl.groups.empty() || wl.groups[0].item_count < 1) return fail(NR_EINVAL, "the plan has no work item");
+    WorkItem *d_first = wl.d_items.as<WorkItem>();
+    NR_CUDA(cudaDeviceSynchronize());
+    if (on) {
+        if (ctx->poisoned.stack >= 0) return fail(NR_EINVAL, "the plan is already poisoned");
+        NR_CUDA(cudaMemcpy(&ctx->poisoned, d_first, sizeof(WorkItem), cudaMemcpyDeviceToHost));
+        WorkItem bad = ctx->poisoned;
+        bad.stack = pl->S;
+        NR_CUDA(cudaMemcpy(d_first, &bad, sizeof(WorkItem), cudaMemcpyHostToDevice));
+    } else {
+        if (ctx->poisoned.stack < 0) return fail(NR_EINVAL, "the plan is not poisoned");
+        NR_CUDA(cudaMemcpy(d_first, &ctx->poisoned, sizeof(WorkItem), cudaMemcpyHostToDevice));
+        NR_CUDA(cudaMemset(wl.d_done.p, 0, wl.d_done.bytes));
+        ctx->poisoned.stack = -1;
+    }
     return NR_OK;
 }
 

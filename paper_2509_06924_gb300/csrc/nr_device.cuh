@@ -440,6 +440,27 @@ __device__ __noinline__ float eq_drain_smem(float2 (*q)[EQ], const int *qj, cons
     return res;
 }
 
+// Slot of a new interior-edge queue entry, and the queue's count after an
+// append: NR_DEBUG builds flag a slot past the CAP-entry queue and keep it
+// (and the count) inside, so an overflow corrupts entries, not memory.
+template <int CAP>
+__device__ __forceinline__ int queue_slot(int slot, int32_t *status)
+{
+    if constexpr (NR_DEBUG) {
+        if (slot >= CAP) {
+            atomicOr(status, NR_FLAG_DEBUG_BOUNDS);
+            return CAP - 1;
+        }
+    }
+    return slot;
+}
+template <int CAP>
+__device__ __forceinline__ int queue_count(int cnt)
+{
+    if constexpr (NR_DEBUG) return cnt < CAP ? cnt : CAP;
+    return cnt;
+}
+
 // Per-stack parameters staged in shared memory, one 16-byte entry per
 // medium, interface and layer (a sweep step reads each with one load).
 template <int NM>

@@ -112,6 +112,12 @@ __global__ void __launch_bounds__(kFp64Block) nr_fp64_kernel(const KernelArgs ka
 {
     __shared__ double sh[kFp64Block / 32];
     const WorkItem wi = ka.items[blockIdx.x];
+    if constexpr (NR_DEBUG) {
+        if (!item_in_bounds(ka, wi, 0)) { // uniform per block
+            if (threadIdx.x == 0) atomicOr(ka.status, NR_FLAG_DEBUG_BOUNDS);
+            return;
+        }
+    }
     const StackInfo si = ka.stacks[wi.stack];
     const int n = si.n;
     const int pert = blockIdx.y;

@@ -83,8 +83,32 @@ struct KernelArgs {
     // FP64 plain path only
     double *ll_pert;     // [(chunk slots) * n_pert] partial chi^2 sums per perturbation
     int32_t n_pert;      // 1, or 2 * max(4n+6) + 1 for central differences
-    int32_t pad;
+    int32_t n_stacks;    // stacks of the batch (checked by NR_DEBUG builds)
 };
+
+// NR_DEBUG builds check on the device every work item a kernel takes (stack
+// index, layer count against the launch's bucket, Q range, chunk index) and
+// every interior-edge queue slot; a failed check sets NR_FLAG_DEBUG_BOUNDS in
+// the status word and skips the access instead of trapping.  Release builds
+// (NR_DEBUG 0) trust the plan, which the host builds from validated metadata.
+#ifndef NR_DEBUG
+#define NR_DEBUG 0
+#endif
+#ifdef __CUDACC__
+// NR_DEBUG: does work item `wi` lie inside the batch?  Its stack index, the
+// stack's layer count against the launch's capacity (nmax = 1: exactly one
+// layer; 0: any count up to NR_MAX_LAYERS), its Q range within the stack's
+// dataset and its chunk among the stack's items.  The stack record is read
+// only once the index is known to be inside the array.
+__device__ __forceinline__ bool item_in_bounds(const KernelArgs &ka, const WorkItem &wi, int nmax)
+{
+    if (wi.stack < 0 || wi.stack >= ka.n_stacks) return false;
+    const StackInfo si = ka.stacks[wi.stack];
+    const bool n_ok = nmax == 1 ? si.n == 1 : si.n >= 0 && si.n <= (nmax ? nmax : NR_MAX_LAYERS);
+    return n_ok && wi.q_lo >= 0 && wi.q_lo <= wi.q_hi && wi.q_hi <= si.nq && wi.chunk >= 0 &&
+           wi.chunk < si.n_chunks;
+}
+#endif
 
 // ---- launchers (nr_mixed.cu) ----
 // Mixed-precision kernels.  `nmax` is the register-array capacity bucket of

@@ -179,6 +179,13 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
         const int item = sh_item;
         if (item >= ka.n_items) break;
         const WorkItem wi = ka.items[item];
+        if constexpr (NR_DEBUG) {
+            if (!item_in_bounds(ka, wi, NMAX)) { // uniform over the block
+                if (tid == 0) atomicOr(ka.status, NR_FLAG_DEBUG_BOUNDS);
+                __syncthreads(); // every thread has read sh_item
+                continue;
+            }
+        }
         const StackInfo si = ka.stacks[wi.stack];
         // the 1-layer bucket holds exactly-1-layer stacks: n is a constant there
         const int n = (NMAX == 1 && NR_EXACT1) ? 1 : si.n;
@@ -567,7 +574,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                         const unsigned em = decltype(EDG)::value ? __ballot_sync(kFull, edge) : 0u;
                         if (em) {
                             if (edge) {
-                                const int slot = eq_cnt + __popc(em & ((1u << lane) - 1u));
+                                const int slot = queue_slot<EQ>(eq_cnt + __popc(em & ((1u << lane) - 1u)), ka.status);
                                 if constexpr (RES) sh_eq[warp][EQF - 1][slot] = make_float2(k0h * wres, 0.f);
                                 if constexpr (T::SMEM_ACC) {
                                     sh_eq[warp][0][slot] = make_float2(k0h, k0l);
@@ -582,7 +589,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
                                 }
                                 sh_eqj[warp][slot] = j;
                             }
-                            eq_cnt += __popc(em);
+                            eq_cnt = queue_count<EQ>(eq_cnt + __popc(em));
                             if constexpr (!T::UNROLL) {
                                 if (eq_cnt >= 32) {
                                     __syncwarp();

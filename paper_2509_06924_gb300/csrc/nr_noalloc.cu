@@ -183,6 +183,7 @@ extern "C" nr_status nr_loglik_grad_noalloc(const nr_batch *b, int32_t n_quad, d
     a.ll_out = loglik;
     a.grad_out = grad;
     a.status = device_flags ? device_flags : d_status;
+    a.n_stacks = S;
     int first = 0;
     for (int g = 0; g < kNumBuckets; ++g) {
         if (count[g] == 0) continue;

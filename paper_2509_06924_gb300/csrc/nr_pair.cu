@@ -422,6 +422,13 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
         const int item = sh_item;
         if (item >= ka.n_items) break;
         const WorkItem wi = ka.items[item];
+        if constexpr (NR_DEBUG) {
+            if (!item_in_bounds(ka, wi, NMAX)) { // uniform over the block
+                if (tid == 0) atomicOr(ka.status, NR_FLAG_DEBUG_BOUNDS);
+                __syncthreads(); // every thread has read sh_item
+                continue;
+            }
+        }
         const StackInfo si = ka.stacks[wi.stack];
         const int n = (NMAX == 1 && NR_EXACT1) ? 1 : si.n;
         const double *p = ka.params + si.par_off;
@@ -762,7 +769,8 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                                     const unsigned em = __ballot_sync(kFull, eh);
                                     if (em) {
                                         if (eh) {
-                                            const int slot = eq_cnt + __popc(em & ((1u << lane) - 1u));
+                                            const int slot =
+                                                queue_slot<EQ>(eq_cnt + __popc(em & ((1u << lane) - 1u)), ka.status);
                                             if constexpr (RES)
                                                 sh_eq[warp][EQF - 1][slot] = make_float2(half(k0h, h) * half(wres, h), 0.f);
                                             if constexpr (ROLL) {
@@ -778,7 +786,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
                                             }
                                             sh_eqj[warp][slot] = j;
                                         }
-                                        eq_cnt += __popc(em);
+                                        eq_cnt = queue_count<EQ>(eq_cnt + __popc(em));
                                         if constexpr (ROLL) {
                                             if (eq_cnt >= 32) {
                                                 __syncwarp();

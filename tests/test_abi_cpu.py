@@ -70,6 +70,15 @@ def test_null_arguments_are_rejected_without_a_device():
     lib.nr_destroy(None)  # no-op
 
 
+def test_release_library_refuses_the_debug_hook():
+    """nr_debug_poison_plan exists only in NR_DEBUG builds: the release
+    library answers NR_EINVAL before touching anything."""
+    lib = nr.load_library()
+    assert not nr.debug_build_selected()
+    assert lib.nr_debug_poison_plan(None, None, 1) == nr.NR_EINVAL
+    assert b"NR_DEBUG" in lib.nr_last_error()
+
+
 def test_create_without_gpu_fails_cleanly():
     import torch
     if torch.cuda.is_available():

@@ -743,6 +743,61 @@ def test_alloc_failure_leaves_context_usable():
     ctx.close()
 
 
+DEBUG_CASES = (("thick_oxide", 64), ("oled_cofit", 8), ("uneven", 40))
+DEBUG_CHILD = r"""
+import sys
+import numpy as np
+import paper_2509_06924_gb300 as nr
+from paper_2509_06924_gb300 import _build, workloads as W
+assert nr.debug_build_selected() and nr.library_path() == _build.DEBUG_LIB
+out = {}
+for name, S in %r:
+    wl = W.make_workload(name, n_stacks=S)
+    ctx = nr.Context(n_quad=wl.n_quad)
+    b = nr.Batch.from_workload(wl)
+    out[name + "_m"] = ctx.reflectivity(b).cpu().numpy().astype(np.float64)
+    ll, g = ctx.loglik_grad(b)
+    f0 = ctx.device_status()
+    ctx.debug_poison_plan(b, True)
+    ctx.loglik_grad(b)
+    f1 = ctx.device_status()
+    ctx.debug_poison_plan(b, False)
+    ll2, g2 = ctx.loglik_grad(b)
+    f2 = ctx.device_status()
+    ctx.close()
+    out[name + "_ll"], out[name + "_g"] = ll.cpu().numpy(), g.cpu().numpy()
+    out[name + "_ll2"], out[name + "_g2"] = ll2.cpu().numpy(), g2.cpu().numpy()
+    out[name + "_flags"] = np.array([f0, f1, f2])
+np.savez(sys.argv[1], **out)
+""" % (DEBUG_CASES,)
+
+
+def test_debug_build_reports_a_corrupted_plan(tmp_path):
+    """The NR_DEBUG library (device bounds checks that set a status flag and
+    skip the access instead of trapping), run in a child process with
+    NR_DEBUG=1: on clean batches of the one-layer, rolled and per-bucket
+    kernels it raises no flag and keeps parity with the oracle; a plan whose
+    first work item names a stack one past the batch (nr_debug_poison_plan)
+    gives NR_FLAG_DEBUG_BOUNDS and no fault; restored, the same plan
+    reproduces the clean results."""
+    import subprocess
+    import sys
+    from paper_2509_06924_gb300 import _build
+    _build.build_debug()
+    out = str(tmp_path / "debug.npz")
+    r = subprocess.run([sys.executable, "-c", DEBUG_CHILD, out], cwd=ROOT, capture_output=True, text=True,
+                       timeout=900, env={**os.environ, "NR_DEBUG": "1"})
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    d = np.load(out)
+    for name, S in DEBUG_CASES:
+        assert list(d[name + "_flags"]) == [0, nr.NR_FLAG_DEBUG_BOUNDS, 0], name
+        wl = W.make_workload(name, n_stacks=S)
+        gpu = {"m": d[name + "_m"], "ll_g": d[name + "_ll"], "g": d[name + "_g"], "flags": 0}
+        assert_parity(wl, gpu, run_oracle(wl))
+        np.testing.assert_allclose(d[name + "_ll2"], d[name + "_ll"], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(d[name + "_g2"], d[name + "_g"], rtol=1e-12, atol=1e-300)
+
+
 def test_waveguide_resonance_stacks():
     """A 520-700 A low-SLD layer between two 300 A high-SLD layers guides
     neutrons between the critical edges of its neighbours: sharp resonances
