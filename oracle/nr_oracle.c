@@ -526,8 +526,9 @@ int oracle_batch(int mode, int n_stacks, const int32_t *n_layers, const double *
     if (bad) { free(par_off); free(out_off); return OR_EINVAL; }
     int status = OR_OK;
 #ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#pragma omp parallel for schedule(dynamic, 1)
+    /* a thread count for this call only (a global setting would outlive it) */
+    const int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
 #endif
     for (int s = 0; s < n_stacks; ++s) {
         const int n = n_layers[s];
