@@ -306,12 +306,107 @@ bool same_meta(const Plan &p, const nr_batch *b, int K)
            std::memcmp(p.q_off.data(), b->q_off, sizeof(int64_t) * (p.D + 1)) == 0;
 }
 
-// Work items per resident CTA below which stacks are cut into Q-range
-// chunks (the persistent queue's tail is then at most 1 / kMinWaves of a launch)
-#ifndef NR_MIN_WAVES
-#define NR_MIN_WAVES 4
-#endif
-constexpr int64_t kMinWaves = NR_MIN_WAVES;
+// Cutting stacks into Q-range chunks.  The register buckets of a work list
+// run concurrently, so their chunk lengths are chosen together: for a bound
+// B on the cost of any one item, every bucket takes its longest chunk (a
+// multiple of its tile, or the whole dataset) whose items stay within B, and
+// the estimated makespan is Graham's bound for longest-first queues, the
+// summed cost of all items / resident CTAs + B.  An item costs (n + 1) x its
+// Q points x K layer-evaluations plus a fixed overhead (queue ticket,
+// staging, reductions, output) of about kItemOverhead layer-evaluations
+// (measured: about 4 us of a CTA's time on the one-layer kernels), twice
+// that for a chunk of a cut stack (partial sums, arrival counter, the last
+// arriver's sum).  The best B must beat whole stacks by 10 %; batches with
+// kChunkWaves stacks per resident CTA keep whole stacks without the search.
+constexpr int64_t kChunkWaves = 8;
+constexpr double kItemOverhead = 1000.0;
+
+struct GroupSpan {
+    int nmax;
+    size_t i0, i1;  // range of `order`
+    int tile_q;
+    int64_t resident;
+};
+
+// One chunk length of a group with its summed item cost, largest item cost
+// and item count
+struct ChunkCand {
+    int64_t chunk;
+    double total, big;
+};
+
+std::vector<int64_t> choose_chunks(const Plan &pl, const std::vector<int> &order, const std::vector<GroupSpan> &gs)
+{
+    std::vector<int64_t> whole(gs.size(), 1);
+    int64_t nst = 0;
+    double res_w = 0.0, w_sum = 0.0;
+    std::vector<std::vector<ChunkCand>> cands(gs.size());
+    const double O = kItemOverhead / std::max(pl.K, 1); // in (n + 1) x Q units
+    auto dlen = [&](int s) { return pl.q_off[pl.dataset[s] + 1] - pl.q_off[pl.dataset[s]]; };
+    auto cost_of = [&](const GroupSpan &g, int64_t chunk) {
+        ChunkCand c{chunk, 0.0, 0.0};
+        for (size_t i = g.i0; i < g.i1; ++i) {
+            const int s = order[i];
+            const int64_t len = dlen(s);
+            const int64_t nch = std::max<int64_t>(1, (len + chunk - 1) / chunk);
+            const double o = nch > 1 ? 2.0 * O : O, w = pl.n_layers[s] + 1.0;
+            c.total += w * (double)len + (double)nch * o;
+            c.big = std::max(c.big, w * (double)std::min(chunk, std::max<int64_t>(len, 1)) + o);
+        }
+        return c;
+    };
+    for (size_t k = 0; k < gs.size(); ++k) {
+        int64_t max_len = 1;
+        for (size_t i = gs[k].i0; i < gs[k].i1; ++i) max_len = std::max(max_len, dlen(order[i]));
+        whole[k] = max_len;
+        nst += (int64_t)(gs[k].i1 - gs[k].i0);
+        const ChunkCand w = cost_of(gs[k], max_len);
+        res_w += w.total * (double)gs[k].resident;
+        w_sum += w.total;
+        cands[k].push_back(w);
+    }
+    // resident CTAs of the concurrent launches: their cost-weighted mean
+    const double R = w_sum > 0.0 ? std::max(1.0, res_w / w_sum) : 1.0;
+    if ((double)nst >= (double)kChunkWaves * R) return whole;
+    for (size_t k = 0; k < gs.size(); ++k)
+        for (int64_t c = gs[k].tile_q; c < whole[k]; c += gs[k].tile_q) cands[k].push_back(cost_of(gs[k], c));
+    // the makespan estimate for a bound B on the largest item
+    auto est = [&](double B, std::vector<int64_t> *pick) {
+        double total = 0.0, big = 0.0;
+        for (size_t k = 0; k < gs.size(); ++k) {
+            const ChunkCand *sel = nullptr;
+            for (const ChunkCand &c : cands[k])
+                if (c.big <= B && (!sel || c.chunk > sel->chunk)) sel = &c;
+            if (!sel) return -1.0;
+            total += sel->total;
+            big = std::max(big, sel->big);
+            if (pick) (*pick)[k] = sel->chunk;
+        }
+        return total / R + big;
+    };
+    double whole_est = 0.0;
+    {
+        double total = 0.0, big = 0.0;
+        for (size_t k = 0; k < gs.size(); ++k) {
+            total += cands[k][0].total;
+            big = std::max(big, cands[k][0].big);
+        }
+        whole_est = total / R + big;
+    }
+    double best_est = whole_est, best_B = -1.0;
+    for (size_t k = 0; k < gs.size(); ++k)
+        for (const ChunkCand &c : cands[k]) {
+            const double e = est(c.big, nullptr);
+            if (e >= 0.0 && e < best_est) {
+                best_est = e;
+                best_B = c.big;
+            }
+        }
+    if (best_B < 0.0 || best_est >= 0.9 * whole_est) return whole;
+    std::vector<int64_t> pick(gs.size(), 1);
+    est(best_B, &pick);
+    return pick;
+}
 
 int tile_for(const nr_ctx *ctx, int mode, int nmax)
 {
@@ -365,40 +460,32 @@ nr_status build_worklist(nr_ctx *ctx, Plan &pl, int mode, WorkList &wl)
         out += pl.q_off[pl.dataset[s] + 1] - pl.q_off[pl.dataset[s]];
     }
     wl.groups.clear();
-    int64_t part = 0;
-    size_t i0 = 0;
-    while (i0 < order.size()) {
+    // the register buckets (ranges of `order`) with their launch shapes
+    std::vector<GroupSpan> spans;
+    for (size_t i0 = 0; i0 < order.size();) {
         size_t i1 = i0;
         const int b = bucket[order[i0]];
         while (i1 < order.size() && bucket[order[i1]] == b) ++i1;
-        Group g;
-        g.nmax = b;
-        g.tile_q = tile_for(ctx, mode, b);
         int occ = 0;
         cudaError_t e = mixed_occupancy(mode, b, ctx->qc.K, &occ);
         if (e != cudaSuccess) return fail(NR_ECUDA, "occupancy query: %s", cudaGetErrorString(e));
-        occ = std::max(occ, 1);
-        const int64_t resident = (int64_t)ctx->sms * occ;
-        const int64_t nst = (int64_t)(i1 - i0);
-        // chunk length: whole datasets unless that leaves fewer than ~4 waves
-        int64_t max_len = 0;
-        for (size_t i = i0; i < i1; ++i) {
-            const int s = order[i];
-            max_len = std::max<int64_t>(max_len, pl.q_off[pl.dataset[s] + 1] - pl.q_off[pl.dataset[s]]);
-        }
-        int64_t chunk = max_len;
-        if (ctx->opt.chunk_q > 0) {
-            chunk = ctx->opt.chunk_q;
-        } else if (nst < kMinWaves * resident && max_len > 0) {
-            const int64_t want = (kMinWaves * resident + nst - 1) / nst; // pieces per stack
-            chunk = std::max<int64_t>((max_len + want - 1) / want, g.tile_q);
-            chunk = (chunk + g.tile_q - 1) / g.tile_q * g.tile_q;
-        }
-        chunk = std::max<int64_t>(chunk, 1);
-        wl.chunk_q = (int)std::min<int64_t>(chunk, 1 << 30);
+        spans.push_back(GroupSpan{b, i0, i1, tile_for(ctx, mode, b), (int64_t)ctx->sms * std::max(occ, 1)});
+        i0 = i1;
+    }
+    std::vector<int64_t> chunks = ctx->opt.chunk_q > 0 ? std::vector<int64_t>(spans.size(), ctx->opt.chunk_q)
+                                                       : choose_chunks(pl, order, spans);
+    int64_t part = 0;
+    wl.chunk_q = 0;
+    for (size_t k = 0; k < spans.size(); ++k) {
+        const GroupSpan &sp = spans[k];
+        Group g;
+        g.nmax = sp.nmax;
+        g.tile_q = sp.tile_q;
+        const int64_t chunk = std::max<int64_t>(chunks[k], 1);
+        wl.chunk_q = std::max(wl.chunk_q, (int)std::min<int64_t>(chunk, 1 << 30));
         g.item_begin = (int)items.size();
         std::vector<std::pair<int64_t, WorkItem>> gi;
-        for (size_t i = i0; i < i1; ++i) {
+        for (size_t i = sp.i0; i < sp.i1; ++i) {
             const int s = order[i];
             const int nq = (int)(pl.q_off[pl.dataset[s] + 1] - pl.q_off[pl.dataset[s]]);
             const int nch = std::max(1, (int)((nq + chunk - 1) / chunk));
@@ -425,11 +512,10 @@ nr_status build_worklist(nr_ctx *ctx, Plan &pl, int mode, WorkList &wl)
         std::stable_sort(gi.begin(), gi.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
         for (auto &x : gi) items.push_back(x.second);
         g.item_count = (int)items.size() - g.item_begin;
-        g.grid = (int)std::min<int64_t>(g.item_count, resident);
+        g.grid = (int)std::min<int64_t>(g.item_count, sp.resident);
         if (ctx->opt.grid_ctas > 0) g.grid = std::min(g.item_count, ctx->opt.grid_ctas);
         g.grid = std::max(g.grid, 1);
         wl.groups.push_back(g);
-        i0 = i1;
     }
     wl.partial_doubles = part;
     NR_CUDA(wl.d_stacks.ensure(sizeof(StackInfo) * std::max(S, 1)));
@@ -620,8 +706,8 @@ std::string tune_key(const nr_ctx *ctx, int mode, int nmax, int items)
 {
     int lg = 0;
     while ((1 << (lg + 1)) <= items) ++lg;
-    char buf[256];
-    snprintf(buf, sizeof buf, "%s|%d|%d|%d|%d|%d|t%d", ctx->gpu_name, ctx->sms, is_grad_mode(mode) ? 2 : 0,
+    char buf[320];
+    snprintf(buf, sizeof buf, "%.200s|%d|%d|%d|%d|%d|t%d", ctx->gpu_name, ctx->sms, is_grad_mode(mode) ? 2 : 0,
              ctx->qc.K, nmax, lg, kTunerVersion);
     return buf;
 }
