@@ -56,12 +56,12 @@ SECONDARY = ("thick_oxide", "oled_cofit", "uneven", "film_1l")
 
 
 # FP32 flops of one table-driven sin/cos (cis_tab): reduction by multiples
-# of 2 pi / 64 (8), remainder polynomial (8), angle addition (6).  A layer
+# of 2 pi / 128 (8), remainder polynomial (6), angle addition (6).  A layer
 # phase E_j already counts its reduction in its 18 flops (double-float phase
-# 7, reduction 8, amplitude and product 3), so it adds 14; a Nevot-Croce
-# factor adds all 22.
-CIS_PHASE = 14
-CIS_NC = 22
+# 7, reduction 8, amplitude and product 3), so it adds 12; a Nevot-Croce
+# factor adds all 20.
+CIS_PHASE = 12
+CIS_NC = 20
 
 
 def flops_per_eval(n: int, K: int) -> float:

@@ -73,9 +73,10 @@ __device__ __forceinline__ void sincos_approx(float x, float &sn, float &cs)
     asm("cos.approx.ftz.f32 %0, %1;" : "=f"(cs) : "f"(x));
 }
 // sin / cos of the layer phases and of the Nevot-Croce factors.
-// NR_SINCOS_TABLE 1: a 64-entry table of cos / sin at multiples of 2 pi / 64
+// NR_SINCOS_TABLE 1: a 128-entry table of cos / sin at multiples of 2 pi / 128
 // (correctly rounded on the host, staged in shared memory) and a short
-// Taylor polynomial for the remainder |x| <= pi / 64 (truncation below 3e-9),
+// Taylor polynomial for the remainder |x| <= pi / 128 (truncation below
+// 1.6e-8, a quarter of an FP32 rounding at 1),
 // combined by the angle-addition formula: about 1e-7 absolute, on the FMA
 // pipe plus one shared load.  0: the special-function unit's sin.approx /
 // cos.approx (about 5e-7 absolute over [-pi, pi]).  Near a waveguide
@@ -92,16 +93,16 @@ __device__ __forceinline__ void sincos_approx(float x, float &sn, float &cs)
 #endif
 
 constexpr int kTabN = kSinCosTabN;
-static_assert(kTabN == 64, "reduction constants are for 64 entries");
-constexpr float kTabScale = 10.18591594696045f;      // 64 / (2 pi)
-constexpr float kTabStepHi = 0.09817477315664291f;   // float(2 pi / 64)
-constexpr float kTabStepLo = -2.7319617679211206e-09f; // 2 pi / 64 - kTabStepHi
+static_assert(kTabN == 128, "reduction constants are for 128 entries");
+constexpr float kTabScale = 20.3718318939209f;        // 128 / (2 pi)
+constexpr float kTabStepHi = 0.04908738657832146f;    // float(2 pi / 128)
+constexpr float kTabStepLo = -1.3659808839605603e-09f; // 2 pi / 128 - kTabStepHi
 
 // (cos, sin) of ph + pl (pl a low-order correction, |pl| << 1): reduction
-// by multiples of 2 pi / 64 (the multiple rounded with the 1.5 * 2^23
+// by multiples of 2 pi / 128 (the multiple rounded with the 1.5 * 2^23
 // addition, whose low mantissa bits are then the table index), remainder
-// polynomial sin x ~ x - x^3 / 6, cos x ~ 1 - x^2 / 2 + x^4 / 24.  tab:
-// cos at [i], sin at [kTabN + i].
+// polynomial sin x ~ x - x^3 / 6, cos x ~ 1 - x^2 / 2.  tab: cos at [i], sin
+// at [kTabN + i].
 __device__ __forceinline__ float2 cis_tab(float ph, float pl, const float *tab)
 {
     const float t = fmaf(ph, kTabScale, kRoundMagic);
@@ -113,7 +114,7 @@ __device__ __forceinline__ float2 cis_tab(float ph, float pl, const float *tab)
     x = __fadd_rn(x, pl);
     const float z = x * x;
     const float sn = fmaf(x * z, -1.f / 6.f, x);
-    const float cn = fmaf(z, fmaf(z, 1.f / 24.f, -0.5f), 1.f);
+    const float cn = fmaf(z, -0.5f, 1.f);
     return make_float2(fmaf(cs.x, cn, -cs.y * sn), fmaf(cs.y, cn, cs.x * sn));
 }
 

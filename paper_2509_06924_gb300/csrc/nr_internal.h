@@ -40,7 +40,7 @@ struct WorkItem {
 };
 
 // Entries of the kernels' sin / cos table (a power of two)
-constexpr int kSinCosTabN = 64;
+constexpr int kSinCosTabN = 128;
 
 // Quadrature rule as the kernels use it: node offset q = Q + dQ * g_k with
 // g_k = x_k / (2 sqrt(ln 2)) as a float pair (hi + lo) and as a double, and

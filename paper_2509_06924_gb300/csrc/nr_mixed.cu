@@ -126,7 +126,7 @@ nr_mixed_kernel(const KernelArgs ka, const QuadConst qc)
     constexpr int EQ = T::EQ_CAP;
 
     __shared__ StackSmem<NM> sm;
-    __shared__ float sh_cs[2 * kTabN];                   // cos, sin at multiples of 2 pi / 64
+    __shared__ float sh_cs[2 * kTabN];                   // cos, sin at multiples of 2 pi / kTabN
     __shared__ __align__(16) float sh_wR[2][2 * BLOCK]; // w_k R per (Q slot, node), double-buffered
     // the super-tile's data per Q point: (Q/2, dQ/2, R_obs, 1/err), and the
     // (residual, smeared R) pairs its tiles leave for the likelihood sums

@@ -117,7 +117,7 @@ __device__ __forceinline__ void pcis_tab(f2 ph, f2 pl, const float *tab, f2 &cs,
     x = padd(x, pl);
     const f2 z = pmul(x, x);
     const f2 sx = pfma(pmul(x, z), bc(-1.f / 6.f), x);
-    const f2 cx = pfma(z, pfma(z, bc(1.f / 24.f), bc(-0.5f)), bc(1.f));
+    const f2 cx = pfma(z, bc(-0.5f), bc(1.f));
     cs = pfma(tc, cx, pneg(pmul(ts, sx)));
     sn = pfma(ts, cx, pmul(tc, sx));
 }
@@ -353,7 +353,7 @@ nr_pair_kernel(const KernelArgs ka, const QuadConst qc)
     static_assert(CAPQ >= 2 * BLOCK / kSubLanes, "a super-tile holds at least one tile");
 
     __shared__ StackSmem<NM> sm;
-    __shared__ float sh_cs[2 * kTabN]; // cos, sin at multiples of 2 pi / 64
+    __shared__ float sh_cs[2 * kTabN]; // cos, sin at multiples of 2 pi / kTabN
     // w_k R per (Q slot, node), double-buffered.  TQ KP <= 4 BLOCK for any K >= 3;
     // the rolled kernels, short of shared memory, take the exact maximum
     // over K >= 3 (408 at K = 5: 51 Q points x 8)

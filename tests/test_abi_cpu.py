@@ -154,13 +154,13 @@ def test_flop_table_is_monotone_and_positive():
     f = [bench.flops_per_eval(n, 21) for n in range(0, 21)]
     assert all(x > 0 for x in f)
     assert all(b > a for a, b in zip(f, f[1:]))
-    # the 1-layer count, term by term: forward 166 + sin/cos 14 + 2 x 22,
+    # the 1-layer count, term by term: forward 166 + sin/cos 12 + 2 x 20,
     # seed 11, adjoint 156 (the 1-layer adjoint keeps the forward's values)
-    assert abs(bench.flops_per_eval(1, 21) - (224 + 11 + 156 + 15 / 21)) < 1e-9
+    assert abs(bench.flops_per_eval(1, 21) - (218 + 11 + 156 + 15 / 21)) < 1e-9
     # the forward count is the gradient's forward sweep plus smearing and
     # likelihood terms, and below the fwd+grad count at every depth
     assert abs(bench.flops_per_eval_fwd(1, 21) - (166 + 2 + 19 / 21)) < 1e-9
-    assert abs(bench.flops_per_eval_fwd(1, 21, table=True) - (224 + 2 + 19 / 21)) < 1e-9
+    assert abs(bench.flops_per_eval_fwd(1, 21, table=True) - (218 + 2 + 19 / 21)) < 1e-9
     assert all(bench.flops_per_eval_fwd(n, 21) < bench.flops_per_eval(n, 21) for n in range(0, 21))
 
 
