@@ -74,9 +74,10 @@ __device__ __forceinline__ void sincos_approx(float x, float &sn, float &cs)
 }
 // sin / cos of the layer phases and of the Nevot-Croce factors.
 // NR_SINCOS_TABLE 1: a 128-entry table of cos / sin at multiples of 2 pi / 128
-// (correctly rounded on the host, staged in shared memory) and a short
-// Taylor polynomial for the remainder |x| <= pi / 128 (truncation below
-// 1.6e-8, a quarter of an FP32 rounding at 1),
+// (correctly rounded on the host, staged in shared memory) and two short
+// polynomials for the remainder |x| <= pi / 128 (sin: x - x^3 / 6, below
+// 1e-10; cos: 1 - c x^2 with c the minimax coefficient on that interval,
+// below 2.6e-9, where the Taylor c = 1/2 leaves a one-sided 1.5e-8),
 // combined by the angle-addition formula: about 1e-7 absolute, on the FMA
 // pipe plus one shared load.  0: the special-function unit's sin.approx /
 // cos.approx (about 5e-7 absolute over [-pi, pi]).  Near a waveguide
@@ -97,12 +98,14 @@ static_assert(kTabN == 128, "reduction constants are for 128 entries");
 constexpr float kTabScale = 20.3718318939209f;        // 128 / (2 pi)
 constexpr float kTabStepHi = 0.04908738657832146f;    // float(2 pi / 128)
 constexpr float kTabStepLo = -1.3659808839605603e-09f; // 2 pi / 128 - kTabStepHi
+// c of cos x ~ 1 - c x^2 minimising the largest error over |x| <= pi / 128
+constexpr float kTabCosC = 0.4999791979789734f;
 
 // (cos, sin) of ph + pl (pl a low-order correction, |pl| << 1): reduction
 // by multiples of 2 pi / 128 (the multiple rounded with the 1.5 * 2^23
 // addition, whose low mantissa bits are then the table index), remainder
-// polynomial sin x ~ x - x^3 / 6, cos x ~ 1 - x^2 / 2.  tab: cos at [i], sin
-// at [kTabN + i].
+// polynomials sin x ~ x - x^3 / 6, cos x ~ 1 - kTabCosC x^2.  tab: cos at
+// [i], sin at [kTabN + i].
 __device__ __forceinline__ float2 cis_tab(float ph, float pl, const float *tab)
 {
     const float t = fmaf(ph, kTabScale, kRoundMagic);
@@ -114,7 +117,7 @@ __device__ __forceinline__ float2 cis_tab(float ph, float pl, const float *tab)
     x = __fadd_rn(x, pl);
     const float z = x * x;
     const float sn = fmaf(x * z, -1.f / 6.f, x);
-    const float cn = fmaf(z, -0.5f, 1.f);
+    const float cn = fmaf(z, -kTabCosC, 1.f);
     return make_float2(fmaf(cs.x, cn, -cs.y * sn), fmaf(cs.y, cn, cs.x * sn));
 }
 

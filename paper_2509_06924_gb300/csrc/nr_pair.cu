@@ -117,7 +117,7 @@ __device__ __forceinline__ void pcis_tab(f2 ph, f2 pl, const float *tab, f2 &cs,
     x = padd(x, pl);
     const f2 z = pmul(x, x);
     const f2 sx = pfma(pmul(x, z), bc(-1.f / 6.f), x);
-    const f2 cx = pfma(z, bc(-0.5f), bc(1.f));
+    const f2 cx = pfma(z, bc(-kTabCosC), bc(1.f));
     cs = pfma(tc, cx, pneg(pmul(ts, sx)));
     sn = pfma(ts, cx, pmul(tc, sx));
 }
