@@ -353,6 +353,27 @@ def test_chunked_matches_unchunked():
     assert_parity(wl, b, run_oracle(wl))
 
 
+def test_chunk_choice_follows_the_makespan_estimate():
+    """Whole stacks where one wave of them nearly fills the GPU (the
+    one-layer film: 1024 stacks, 760 resident CTAs; a chunk's fixed cost
+    outweighs the shorter tail), Q-range chunks where a few deep stacks
+    would leave most CTAs idle; every Q point is covered exactly once
+    either way, so the chunked plan keeps parity."""
+    film = W.make_workload("film_1l")
+    ctx = nr.Context(n_quad=film.n_quad)
+    bf = nr.Batch.from_workload(film)
+    groups = ctx.plan_groups(bf, grad=True)
+    assert sum(g["items"] for g in groups) == film.n_stacks
+    wl = W.make_workload("vi_step", n_stacks=4)             # 12 stacks of 12 layers x 300 Q
+    ctx2 = nr.Context(n_quad=wl.n_quad)
+    b = nr.Batch.from_workload(wl)
+    groups = ctx2.plan_groups(b, grad=True)
+    assert sum(g["items"] for g in groups) > 4 * wl.n_stacks
+    ctx.close()
+    ctx2.close()
+    assert_parity(wl, run_gpu(wl), run_oracle(wl))
+
+
 def test_host_memory_calls_match_device_calls():
     wl = W.make_workload("uneven", n_stacks=20)
     ctx = nr.Context(n_quad=wl.n_quad)
