@@ -14,7 +14,8 @@
 //   vi_adam:   the gradient of the single-sample negative ELBO (Eqs. 22-24,
 //              e held fixed: d/d mu = -g, d/d L_ij = -g_i e_j,
 //              d/d log L_ii = -g_i e_i L_ii - 1) and one Adam step of every
-//              entry of phi, one thread per entry; the ELBO estimate
+//              entry of phi (one block per restart, the moments and the step
+//              in FP32 arithmetic on FP64 storage); the ELBO estimate
 //              log pi(u) + (the part above) is written per restart.
 #include <cuda_runtime.h>
 
@@ -61,37 +62,53 @@ __global__ void vi_sample_kernel(const double *phi, const double *eps, int R, in
     if (lane == 0) part[r] = acc;
 }
 
+// One block per restart.  The restart's gradient and draw are staged as
+// floats in shared memory (when P <= kAdamStageP), and the moments and the
+// step are formed in FP32 arithmetic: phi, m and v keep their FP64 storage,
+// so phi accumulates its updates at full precision, while the update itself
+// (a heuristic scaling of the gradient, whose own error is ~1e-5) needs no
+// more than FP32.  In FP64 the square root and division alone bound this
+// kernel on GB300's FP64 rate.
+constexpr int kAdamStageP = 4096;
+
 __global__ void vi_adam_kernel(double *phi, double *m, double *v, const double *eps, const double *g,
-                               const double *logp, const double *part, int R, int P, int64_t nphi,
-                               const double *bias, double lr, double beta1, double beta2, double eps_adam,
-                               double *elbo)
+                               const double *logp, const double *part, int P, int64_t nphi, const double *bias,
+                               float lr, float beta1, float beta2, float eps_adam, bool stage, double *elbo)
 {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)R * nphi) return;
-    const int r = (int)(idx / nphi);
-    const int64_t p = idx - (int64_t)r * nphi;
-    const double *gr = g + (int64_t)r * P;
-    double grad;
-    if (p < P) {
-        grad = -gr[p];
-    } else {
-        // packed triangle index -> (i, j): i (i + 1) / 2 <= q < (i + 1) (i + 2) / 2
-        const int64_t q = p - P;
-        int i = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f); // corrected below
-        while ((int64_t)(i + 1) * (i + 2) / 2 <= q) ++i;
-        while ((int64_t)i * (i + 1) / 2 > q) --i;
-        const int j = (int)(q - (int64_t)i * (i + 1) / 2);
-        const double *e = eps + (int64_t)r * P;
-        grad = (i == j) ? -gr[i] * e[i] * exp(phi[idx]) - 1.0 : -gr[i] * e[j];
+    extern __shared__ float sh_ge[]; // g_r [P], eps_r [P]
+    const int r = blockIdx.x;
+    const double *gr = g + (int64_t)r * P, *er = eps + (int64_t)r * P;
+    if (stage) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            sh_ge[i] = (float)gr[i];
+            sh_ge[P + i] = (float)er[i];
+        }
+        __syncthreads();
     }
-    const double mm = beta1 * m[idx] + (1.0 - beta1) * grad;
-    const double vv = beta2 * v[idx] + (1.0 - beta2) * grad * grad;
-    m[idx] = mm;
-    v[idx] = vv;
-    const double mh = mm * bias[0];
-    const double vh = vv * bias[1];
-    phi[idx] -= lr * mh / (sqrt(vh) + eps_adam);
-    if (p == 0 && elbo) elbo[r] = logp[r] + part[r];
+    auto gi = [&](int i) { return stage ? sh_ge[i] : (float)gr[i]; };
+    auto ej = [&](int j) { return stage ? sh_ge[P + j] : (float)er[j]; };
+    const float c0 = (float)bias[0], c1 = (float)bias[1];
+    double *phr = phi + (int64_t)r * nphi, *mr = m + (int64_t)r * nphi, *vr = v + (int64_t)r * nphi;
+    for (int64_t p = threadIdx.x; p < nphi; p += blockDim.x) {
+        float grad;
+        if (p < P) {
+            grad = -gi((int)p);
+        } else {
+            // packed triangle index -> (i, j): i (i + 1) / 2 <= q < (i + 1) (i + 2) / 2
+            const int64_t q = p - P;
+            int i = (int)((sqrtf(8.f * (float)q + 1.f) - 1.f) * 0.5f); // corrected below
+            while ((int64_t)(i + 1) * (i + 2) / 2 <= q) ++i;
+            while ((int64_t)i * (i + 1) / 2 > q) --i;
+            const int j = (int)(q - (int64_t)i * (i + 1) / 2);
+            grad = (i == j) ? -gi(i) * ej(i) * expf((float)phr[p]) - 1.f : -gi(i) * ej(j);
+        }
+        const float mm = fmaf(beta1, (float)mr[p], (1.f - beta1) * grad);
+        const float vv = fmaf(beta2, (float)vr[p], (1.f - beta2) * grad * grad);
+        mr[p] = mm;
+        vr[p] = vv;
+        phr[p] -= (double)(lr * (mm * c0) / (sqrtf(vv * c1) + eps_adam));
+    }
+    if (threadIdx.x == 0 && elbo) elbo[r] = logp[r] + part[r];
 }
 
 } // namespace
@@ -110,10 +127,11 @@ cudaError_t launch_vi_adam(double *phi, double *m, double *v, const double *eps,
                            double beta1, double beta2, double eps_adam, double *elbo, cudaStream_t st)
 {
     const int64_t nphi = (int64_t)P + (int64_t)P * (P + 1) / 2;
-    const int64_t n = (int64_t)R * nphi;
-    if (n == 0) return cudaSuccess;
-    vi_adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(phi, m, v, eps, g, logp, part, R, P, nphi, bias,
-                                                                 lr, beta1, beta2, eps_adam, elbo);
+    if (R == 0 || nphi == 0) return cudaSuccess;
+    const bool stage = P <= kAdamStageP;
+    const size_t smem = stage ? sizeof(float) * 2 * (size_t)P : 0;
+    vi_adam_kernel<<<R, 256, smem, st>>>(phi, m, v, eps, g, logp, part, P, nphi, bias, (float)lr, (float)beta1,
+                                         (float)beta2, (float)eps_adam, stage, elbo);
     return cudaGetLastError();
 }
 
