@@ -369,7 +369,10 @@ std::vector<int64_t> choose_chunks(const Plan &pl, const std::vector<int> &order
     const double R = w_sum > 0.0 ? std::max(1.0, res_w / w_sum) : 1.0;
     if ((double)nst >= (double)kChunkWaves * R) return whole;
     for (size_t k = 0; k < gs.size(); ++k)
-        for (int64_t c = gs[k].tile_q; c < whole[k]; c += gs[k].tile_q) cands[k].push_back(cost_of(gs[k], c));
+        // chunk lengths of 1..16 tiles, then growing by a quarter (a few
+        // dozen candidates however long the datasets are)
+        for (int64_t mt = 1; mt * gs[k].tile_q < whole[k]; mt = mt < 16 ? mt + 1 : mt + (mt + 3) / 4)
+            cands[k].push_back(cost_of(gs[k], mt * gs[k].tile_q));
     // the makespan estimate for a bound B on the largest item
     auto est = [&](double B, std::vector<int64_t> *pick) {
         double total = 0.0, big = 0.0;
